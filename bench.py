@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark of the population-annealing hot path on one GB300 (or N, one run per GPU).
+
+Workload (the headline configuration): 2D Ising ferromagnet, L=64 periodic,
+R=100000 replicas, beta from 0 to 1 in 200 equal steps, theta=10 Metropolis
+sweeps per step, one run for each of the five copy-count rules (multinomial,
+systematic, residual, Poisson, nearest-integer), Philox seed 7.  One benchmark
+"step" is one temperature step of one run (reweighting, Q, copy counts, scan,
+gather, theta sweeps, measurements); the default 1000 steps are the five runs
+back to back.  Inputs are synthetic (the method draws its own initial state).
+
+Printed: one JSON line on rank 0.  `value` is spin updates per ns over the
+timed steps (device time, CUDA events on the library's stream, L2 flushed
+between steps); `roofline` relates the sweep kernel's integer throughput to
+the SM issue peak; `e2e` times the same runs through the C ABI from host
+arrays to host results; `cpu_baseline` times the CPU oracle on a bounded
+sample of the same workload.
+
+--impl reference times the CPU oracle itself as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("spin updates/ns and PA steps/s at 1 GB300 vs roofline; "
+          "time-to-1e-4 free-energy error")
+UNIT = "spin updates/ns"
+RULES = ["multinomial", "systematic", "residual", "poisson", "nearest"]
+L, DIM, R, NSTEPS, THETA, SEED, BETA_F = 64, 2, 100_000, 200, 10, 7, 1.0
+WORKLOAD = ("2D Ising ferromagnet L=64 periodic, R=100000, beta 0->1 in 200 steps, theta=10, "
+            "multinomial/systematic/residual/Poisson/nearest-integer runs, seed 7")
+# integer operations per spin update that the method itself requires: a quarter
+# of a Philox4x32-10 block (10 rounds x (2 wide multiplies + 2 three-input XORs)
+# = 40 operations per 4 draws) and the threshold compare
+OPS_PER_UPDATE = 11.0
+INT_LANES_PER_SM = 128  # 4 schedulers x 32 lanes issue one integer op per clock each
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _sweep_traffic(kernel_src_hash):
+    """DRAM bytes per sweep launch from a committed ncu capture of the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    if d.get("kernel_source_sha256") != kernel_src_hash:
+        return None
+    return d.get("dram_bytes_per_full_launch")
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    for f in ("pa_sweep.cu", "pa_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2401_07965_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------------------------
+
+def oracle_sample(R_s, n_steps_s, rule="systematic"):
+    """Time the CPU oracle: a population of R_s replicas of the benchmark lattice through the
+    first n_steps_s temperature steps of the benchmark schedule.  Returns (updates, seconds)."""
+    from oracle import oracle as O
+    O.build()
+    betas = np.linspace(0.0, BETA_F, NSTEPS + 1)
+    thetas = np.full(NSTEPS, THETA, np.uint32)
+    run = O.Run(DIM, L, O.ferro_couplings(DIM, L), R_s, betas, thetas, O.RESAMPLERS[rule], SEED,
+                R_cap=4 * R_s)
+    upd = 0
+    t0 = time.perf_counter()
+    for _ in range(n_steps_s):
+        assert run.step() == 0
+        upd += THETA * L * L * run.size
+    return upd, time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    R_s = 32
+    # warm-up
+    for _ in range(args.warmup):
+        oracle_sample(R_s, 1)
+    upd_tot, sec_tot = 0, 0.0
+    for k in range(args.steps):
+        u, s = oracle_sample(R_s, 1, RULES[k % 5])
+        upd_tot += u
+        sec_tot += s
+    v = upd_tot / (sec_tot * 1e9)
+    sample = (f"each step: the CPU oracle (single thread) runs {R_s} replicas of the L=64 "
+              f"lattice through one temperature step (resampling + theta=10 sweeps), rules "
+              f"cycled over the five")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec_tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_replicas": R_s},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2401_07965_gb300 import pa
+
+    betas = np.linspace(0.0, BETA_F, NSTEPS + 1)
+    thetas = np.full(NSTEPS, THETA, np.uint32)
+    seed = SEED + 1000 * rank
+    stream = torch.cuda.current_stream(dev)
+
+    # warm-up on a throw-away run of the same shape
+    wu = pa.Population(DIM, L, R, betas, thetas, "systematic", seed + 99, stream=stream)
+    wu.step(max(args.warmup, 1))
+    wu.observables()
+    wu.close()
+
+    # timed: runs of the five rules back to back, one temperature step per bench step
+    runs = []
+    plan = []
+    remaining = args.steps
+    r = 0
+    while remaining > 0:
+        rule = RULES[r % 5]
+        n = min(NSTEPS, remaining)
+        plan.append((rule, n))
+        remaining -= n
+        r += 1
+    for rule, n in plan:
+        runs.append(pa.Population(DIM, L, R, betas, thetas, rule, seed, stream=stream))
+    for p in runs:
+        pa.pa_enable_timing(p.ctx, True)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches0 = sum(pa.pa_launch_count(p.ctx) for p in runs)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        k = 0
+        for (rule, n), p in zip(plan, runs):
+            for _ in range(n):
+                flush.fill_(k & 0xFF)          # L2 flush, outside the step's events
+                ev[k][0].record(stream)
+                p.step(1)
+                ev[k][1].record(stream)
+                k += 1
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    launches = sum(pa.pa_launch_count(p.ctx) for p in runs) - launches0
+    updates = 0.0
+    sweep_ms, sweep_n, sweep_upd = 0.0, 0, 0.0
+    for (rule, n), p in zip(plan, runs):
+        tr = p.trace()
+        updates += sum(THETA * L * L * row["R_i"] for row in tr[1:n + 1])
+        ms, cnt, u = pa.pa_sweep_timing(p.ctx)
+        sweep_ms += ms
+        sweep_n += cnt
+        sweep_upd += u
+    total_ms = sum(step_ms)
+    # max over ranks of the device time; sum of the units
+    if world > 1:
+        t = torch.tensor([total_ms, updates], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        total_ms, updates = float(mx[0]), float(t[1])
+    value = updates / (total_ms * 1e6)
+    for p in runs:
+        p.close()
+    del flush
+
+    # end to end through the C ABI from host inputs to host results
+    e2e = run_e2e(args, pa, stream, seed, dev)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    peaks, peak_src = _peaks()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clocks = clk.summary()
+    f_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak_tops = nsm * INT_LANES_PER_SM * f_hz / 1e12
+    sweep_rate = sweep_upd / (sweep_ms * 1e6)  # updates / ns inside the sweep kernel
+    achieved = OPS_PER_UPDATE * sweep_rate * 1e9 / 1e12
+    traffic_full = _sweep_traffic(_src_hash())
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+            "frac": achieved / peak_tops, "traffic": traffic_full,
+            "kernel": "k_group<2,false> (copy + theta sweeps + measurement)",
+            "peak_source": f"{nsm} SMs x {INT_LANES_PER_SM} int lanes x sm_max_mhz "
+                           f"({peak_src} clocks)",
+            "ops_per_update": OPS_PER_UPDATE, "sweep_updates_per_ns": sweep_rate,
+            "sweep_share_of_step_time": sweep_ms / total_ms if world == 1 else None}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        u, s = oracle_sample(256, 6)
+        cpu = {"value": u / (s * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "CPU oracle (single thread, one int8 per spin) on 256 replicas of the "
+                         "L=64 lattice through the first 6 temperature steps of the schedule "
+                         "(theta=10, systematic), %.2e updates in %.1f s" % (u, s)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "pa_steps_per_s": 1e3 * args.steps / total_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (initial population drawn by the method at beta=0)",
+            "config": {"workload": WORKLOAD, "rules": [r for r, _ in plan],
+                       "l2": "flushed between steps (256 MiB write, outside the step events)",
+                       "parallelism": f"{world} independent runs" if world > 1 else "1 run"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, pa, stream, seed, dev):
+    """Whole runs through the C ABI: host schedule -> pa_init -> per step pa_step +
+    pa_observables (device -> host) -> pa_free_energy.  Host wall clock."""
+    import ctypes as C
+    import torch
+    betas = np.linspace(0.0, BETA_F, NSTEPS + 1)
+    thetas = np.full(NSTEPS, THETA, np.uint32)
+    n_total = args.steps
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    updates = 0.0
+    done = 0
+    r = 0
+    h2d = 0
+    d2h = 0
+    while done < n_total:
+        rule = RULES[r % 5]
+        n = min(NSTEPS, n_total - done)
+        ctx = pa.pa_init(DIM, L, ("ferro",), R, 0, betas, thetas, pa.RESAMPLERS[rule], seed,
+                         stream.cuda_stream)
+        h2d += betas.nbytes + thetas.nbytes + 3 * 8 * NSTEPS + 16 * NSTEPS
+        for _ in range(n):
+            pa.pa_step(ctx, 1)
+            o = pa.pa_observables(ctx)
+            d2h += C.sizeof(pa.pa_obs)
+            updates += THETA * L * L * o["R_i"]
+        pa.pa_free_energy(ctx)
+        pa.pa_destroy(ctx)
+        done += n
+        r += 1
+    sec = time.perf_counter() - t0
+    return {"value": updates / (sec * 1e9), "unit": UNIT,
+            "h2d_bytes_per_step": h2d / n_total, "d2h_bytes_per_step": d2h / n_total,
+            "what": "pa_init from host arrays, then pa_step + pa_observables per step, "
+                    "pa_free_energy per run; host wall clock including init"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

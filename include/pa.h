@@ -1,0 +1,199 @@
+/*
+ * pa.h -- C ABI of the GB300 population-annealing library (libpa.so).
+ *
+ * Population annealing (PA), Sec. 2 of Ebert, Gessert, Janke & Weigel,
+ * "Optimized population Monte Carlo" (arXiv:2401.07965): a population of R
+ * replicas of a periodic Ising / Edwards-Anderson +-J lattice is cooled from
+ * beta_0 = 0 to beta_f in steps.  Each temperature step i
+ *   (a) reweights replica j by exp(-(beta_i - beta_{i-1}) E_j), normalised by
+ *       Q_i of Eq. (Q),
+ *   (b) draws integer copy numbers r_j with <r_j> = tau_j (Sec. 3) by one of
+ *       five rules and replicates the population accordingly (with families),
+ *   (c) runs theta_i checkerboard Metropolis sweeps on every replica at beta_i,
+ *   (d) measures population averages (step 4) and accumulates
+ *       -beta_i F_i = ln Z_0 + sum_k ln Q_k (Eq. free-energy-estimator).
+ * All of (a)-(d) run in CUDA kernels on the device that owns the stream.
+ *
+ * Conventions
+ *  - Every call returns pa_status; nothing else crosses the ABI (no C++
+ *    exceptions, no device traps).  Kernels report errors through a device
+ *    status word that the next synchronising call (pa_sync, pa_observables,
+ *    pa_free_energy, pa_get_array) returns.  After any error other than
+ *    PA_ERR_ARG the context only accepts pa_destroy and the query calls.
+ *  - Host arrays passed in are read during the call and copied; the caller
+ *    keeps ownership.  Device memory is either a caller-provided workspace
+ *    (pa_workspace_bytes tells its size; the library then allocates nothing
+ *    on the device) or, if workspace == NULL, allocated by pa_init and freed
+ *    by pa_destroy.
+ *  - Work is enqueued on the caller's CUDA stream (NULL = legacy default).
+ *    pa_step is asynchronous.  A context must not be used from two host
+ *    threads at once.
+ *  - Lattice: dim in {2,3}, L even, 2 <= L, N = L^dim <= 2^20 sites,
+ *    periodic; site s = x + L*y (+ L*L*z).  Spins are stored one bit per
+ *    site, bit (s & 31) of word (s >> 5), bit value 1 meaning sigma = -1.
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pa_ctx pa_ctx;
+
+typedef enum {
+    PA_OK = 0,
+    PA_ERR_ARG = 1,           /* invalid argument; the context is unchanged            */
+    PA_ERR_CUDA = 2,          /* a CUDA runtime call failed                             */
+    PA_ERR_NOMEM = 3,         /* device allocation failed or workspace too small        */
+    PA_ERR_CAPACITY = 4,      /* variable-size resampling produced R_i > R_cap          */
+    PA_ERR_POISSON_KMAX = 5,  /* a Poisson inversion exceeded 256 per chunk (p < 1e-300)*/
+    PA_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                          */
+    PA_ERR_STATE = 7,         /* the context holds an earlier device error              */
+    PA_ERR_DONE = 8           /* the schedule has no further temperature step           */
+} pa_status;
+
+/* Copy-count rules of Sec. 3.  Multinomial, systematic and residual keep
+ * R_i = R; Poisson and nearest-integer let R_i fluctuate and use the rescaled
+ * factors tau-hat = (R / R_{i-1}) tau of Eq. (taus). */
+typedef enum {
+    PA_MULTINOMIAL = 0,  /* R labels iid uniform on the weight axis (Fig. 2a)       */
+    PA_SYSTEMATIC = 1,   /* one uniform offset, labels spaced by one (Fig. 2b)       */
+    PA_RESIDUAL = 2,     /* floor(tau) copies + multinomial draws on the remainders  */
+    PA_POISSON = 3,      /* r_j ~ Poisson(tau-hat_j)                                 */
+    PA_NEAREST = 4       /* floor(tau-hat) copies + 1 with prob. tau-hat - floor     */
+} pa_resampler;
+
+typedef struct {
+    int32_t dim; /* 2 or 3 */
+    int32_t L;   /* even, >= 2 */
+} pa_lattice;
+
+typedef enum {
+    PA_COUPLING_FERRO = 0,    /* J = +1 on every bond (Eq. Hamiltonian)               */
+    PA_COUPLING_EA_PM = 1,    /* J = +-1 iid with p = 1/2 from (disorder_seed, realization) */
+    PA_COUPLING_EXPLICIT = 2  /* J[a*N + s] in {+1,-1} for the bond (s, s + e_a)       */
+} pa_coupling_kind;
+
+typedef struct {
+    int32_t kind;            /* pa_coupling_kind                                   */
+    uint32_t realization;    /* EA: disorder realization index                     */
+    uint64_t disorder_seed;  /* EA: Philox key of the couplings                     */
+    const int8_t *J;         /* EXPLICIT: host array of dim*N values (+1 or -1)     */
+} pa_couplings;
+
+/* Annealing schedule (Sec. 2 steps 1-5): beta[0] = 0 (exact sampling of the
+ * initial population), beta strictly increasing, theta[i-1] >= 0 sweeps at
+ * beta[i].  Copied at pa_init. */
+typedef struct {
+    int32_t n_steps;        /* number of temperature steps n >= 1                 */
+    const double *beta;     /* host, n_steps + 1 values                            */
+    const uint32_t *theta;  /* host, n_steps values, each < 2^26                   */
+} pa_schedule;
+
+/* Population averages after the sweeps of the current step (Sec. 2 step 4).
+ * Integer sums are exact; e = <E>/N, m = M/N. */
+typedef struct {
+    int32_t step;          /* completed temperature steps i                         */
+    uint32_t R_i;          /* population size after step i                         */
+    uint32_t R_prev;       /* population size before the resampling of step i      */
+    uint32_t pad0;
+    double beta;           /* beta_i                                                */
+    double lnQ;            /* ln Q_i of Eq. (Q)                                     */
+    double sum_lnQ;        /* sum_{k<=i} ln Q_k                                      */
+    int64_t sumE, sumE2, sumAbsM, sumM2;
+    int64_t sumC2;         /* sum over families k of c_k^2 (c_k = members)          */
+    uint64_t accepts;      /* accepted Metropolis flips during step i               */
+    double entropy;        /* -sum_k (c_k/R_i) ln(c_k/R_i)                           */
+    double sv;             /* sampling variance, Eq. (sv), over the R_prev parents  */
+    double e, e2, absm, m2;/* <E>/N, <E^2>/N^2, <|M|>/N, <M^2>/N^2                 */
+    double c;              /* specific heat per spin beta^2 N (<e^2> - <e>^2)        */
+    double chi;            /* susceptibility per spin beta N (<m^2> - <|m|>^2)        */
+    double rho_t;          /* family statistic of Eq. (rho_t), sum c_k^2 / R_i       */
+    double accept_rate;    /* accepts / (theta_i N R_i)                             */
+} pa_obs;
+
+/* Arrays readable with pa_get_array. */
+typedef enum {
+    PA_ARRAY_SPINS = 0,      /* uint32 [R_i][ceil(N/32)] packed spins              */
+    PA_ARRAY_ENERGY = 1,     /* int32  [R_i]                                       */
+    PA_ARRAY_FAMILY = 2,     /* uint32 [R_i] index of the initial ancestor         */
+    PA_ARRAY_COUNTS = 3,     /* uint32 [R_prev] copy numbers r_j of the last step  */
+    PA_ARRAY_ANCESTOR = 4,   /* uint32 [R_i] parent slot j of each new slot        */
+    PA_ARRAY_MAGNET = 5      /* int32  [R_i] magnetisation M = sum sigma           */
+} pa_array;
+
+/* Bytes of device workspace a context needs (0 on invalid arguments).
+ * R_cap = 0 selects the default capacity R + ceil(10 sqrt(R)) + 64 for the
+ * variable-size rules and R for the fixed-size ones. */
+size_t pa_workspace_bytes(const pa_lattice *lat, uint32_t R, uint32_t R_cap, int32_t n_steps,
+                          pa_resampler resampler);
+
+/* Create a context and draw the initial population at beta_0 = 0 (Sec. 2
+ * step 1: every replica iid uniform, family_j = j, R_0 = R).
+ * seed: 64-bit Philox key of every draw of the run.
+ * cuda_stream: a cudaStream_t (may be NULL).
+ * workspace / workspace_bytes: optional caller-owned device memory (256-byte
+ * aligned, at least pa_workspace_bytes) or NULL / 0.
+ * Errors: PA_ERR_ARG (bad lattice, R == 0, R_cap < R, schedule not starting
+ * at 0 or not increasing, theta too large), PA_ERR_NOMEM, PA_ERR_CUDA. */
+pa_status pa_init(pa_ctx **out, const pa_lattice *lat, const pa_couplings *cpl, uint32_t R,
+                  uint32_t R_cap, const pa_schedule *sched, pa_resampler resampler,
+                  uint64_t seed, void *cuda_stream, void *workspace, size_t workspace_bytes);
+
+/* Enqueue n temperature steps (Sec. 2 steps 2-4 each).  Asynchronous.
+ * Returns PA_ERR_DONE without enqueuing anything if fewer than n steps remain. */
+pa_status pa_step(pa_ctx *ctx, int32_t n);
+
+/* Wait for the stream and return the device status word. */
+pa_status pa_sync(pa_ctx *ctx);
+
+/* Synchronise and fill *out for the current step. */
+pa_status pa_observables(pa_ctx *ctx, pa_obs *out);
+
+/* Synchronise and fill rows[0..min(max_rows, step+1)) with the observables of
+ * steps 0..step (step 0 = the initial population); *n_rows receives the count. */
+pa_status pa_trace(pa_ctx *ctx, pa_obs *rows, int32_t max_rows, int32_t *n_rows);
+
+/* Synchronise and return -beta_i F_i = N ln 2 + sum_k ln Q_k
+ * (Eq. free-energy-estimator with ln Z_0 = N ln 2) and F_i / N
+ * (NaN at beta = 0). */
+pa_status pa_free_energy(pa_ctx *ctx, double *minus_beta_F, double *f_per_spin);
+
+/* Synchronise and copy one state array to host memory.  capacity is in
+ * elements (words for PA_ARRAY_SPINS); *n_out receives the element count
+ * written.  PA_ERR_ARG if capacity is too small. */
+pa_status pa_get_array(pa_ctx *ctx, pa_array which, void *host, size_t capacity, size_t *n_out);
+
+/* Checkpoint restore: replace the population by R_i replicas of packed spins
+ * (host, [R_i][ceil(N/32)] words) and families (host, may be NULL for j),
+ * and set the completed step count and the running sum of ln Q.  Energies and
+ * magnetisations are recomputed on the device.  Because every draw is keyed
+ * by (seed, step, slot, site), a restored run continues bit for bit like the
+ * uninterrupted one. */
+pa_status pa_set_state(pa_ctx *ctx, const uint32_t *spins, const uint32_t *family, uint32_t R_i,
+                       int32_t step, double sum_lnQ);
+
+/* Kernel timing for roofline accounting.  When enabled, every following
+ * sweep launch is bracketed by CUDA events on the context's stream.
+ * pa_sweep_timing synchronises and returns the summed sweep-kernel time in
+ * milliseconds, the number of timed launches and the spin updates they did. */
+pa_status pa_enable_timing(pa_ctx *ctx, int32_t on);
+pa_status pa_sweep_timing(pa_ctx *ctx, double *ms, int64_t *launches, double *updates);
+
+/* Number of kernels this context has launched so far. */
+int64_t pa_launch_count(const pa_ctx *ctx);
+
+/* Release the context (and the device memory it allocated).  NULL is a no-op. */
+pa_status pa_destroy(pa_ctx *ctx);
+
+const char *pa_strerror(pa_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_H */

@@ -598,7 +598,8 @@ int or_run_step(or_run *r)
     st = or_resample(r->E, Rprev, r->R, dbeta, r->method, r->seed, (uint32_t)i,
                      r->counts, r->f_rep, &lnQ, &Rnew);
     if (st) { r->status = st; return st; }
-    if (Rnew > r->Rcap) { r->status = OR_ERR_CAP; return OR_ERR_CAP; }
+    /* a population that outgrows its capacity, or dies out, stops the run */
+    if (Rnew > r->Rcap || Rnew == 0) { r->status = OR_ERR_CAP; return OR_ERR_CAP; }
     d = 0;
     for (j = 0; j < Rprev; ++j) {
         uint32_t c;

@@ -1,0 +1,138 @@
+// pa_internal.cuh -- device-side definitions shared by the library's kernels.
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), keyed
+// by the 64-bit run seed; the counter (c0, c1, c2, c3) carries the draw's
+// purpose in the top nibble of c1:
+//   sweep      c0 = site quad, c1 = (sweep << 1) | colour, c2 = step, c3 = slot
+//   init       c0 = word >> 2, c1 = 1 << 28,             c2 = 0,    c3 = replica
+//   resample   c0 = index,     c1 = (2 << 28) | rule,    c2 = step, c3 = chunk
+//   disorder   c0 = bond >> 7, c1 = 3 << 28,             c2 = 0,    c3 = realization
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pa {
+
+constexpr uint32_t PHILOX_M0 = 0xD2511F53u;
+constexpr uint32_t PHILOX_M1 = 0xCD9E8D57u;
+constexpr uint32_t PHILOX_W0 = 0x9E3779B9u;
+constexpr uint32_t PHILOX_W1 = 0xBB67AE85u;
+
+constexpr uint32_t DOM_SWEEP = 0x00000000u;
+constexpr uint32_t DOM_INIT = 0x10000000u;
+constexpr uint32_t DOM_RESAMPLE = 0x20000000u;
+constexpr uint32_t DOM_DISORDER = 0x30000000u;
+constexpr uint32_t RULE_NEAREST = 0u, RULE_SYSTEMATIC = 1u, RULE_MULTINOMIAL = 2u,
+                   RULE_RESIDUAL = 3u, RULE_POISSON = 4u;
+
+constexpr int FRAC_BITS = 40;          // tau-hat is carried as a 2^-40 fixed-point integer
+constexpr uint32_t POISSON_KMAX = 256; // per chunk of mean <= 16
+
+enum Method { M_MULTINOMIAL = 0, M_SYSTEMATIC = 1, M_RESIDUAL = 2, M_POISSON = 3, M_NEAREST = 4 };
+
+enum DevStatus { S_OK = 0, S_CAPACITY = 4, S_KMAX = 5, S_TIMEOUT = 6 };
+
+struct uint4x {
+    uint32_t x, y, z, w;
+};
+
+// One Philox4x32-10 block.  Usable on host (couplings) and device.
+__host__ __device__ __forceinline__ uint4x philox(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                  uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)PHILOX_M0 * c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// Device state shared by the kernels of a run (one per context).
+struct DevState {
+    int32_t step;      // completed temperature steps
+    int32_t status;    // DevStatus
+    uint32_t R_cur;    // current population size
+    uint32_t R_prev;   // size that the last resampling started from
+    double sum_lnQ;    // running sum of ln Q_k
+    uint32_t lmin;     // lowest occupied energy level of the last resampling
+    uint32_t K;        // number of levels spanned
+    uint64_t T;        // sum of fixed-point weights f_j
+    uint64_t Tres;     // sum of their fractional parts (residual rule)
+    uint64_t Rres;     // residual draws
+    uint64_t pad[2];
+};
+
+// Per-step accumulators, device-resident (row i = after temperature step i).
+struct TraceRow {
+    double lnQ;
+    double sum_lnQ;
+    double c_ln_c;   // sum_k c_k ln c_k over families
+    double sv_sum;   // sum_j (r_j - f_j 2^-40)^2 over parents
+    unsigned long long sumE, sumE2, sumAbsM, sumM2, sumC2, accepts;  // two's complement
+    uint32_t R_i, R_prev;
+    uint64_t pad;
+};
+
+// Everything a kernel needs, passed by value.
+struct KParams {
+    int d, L, N, W, Wp;      // lattice; W words per replica, Wp padded to 4
+    int nlev;                // d*N/2 + 1 histogram levels (level = U >> 1)
+    int parity;              // U mod 2, the same for every configuration
+    int ea;                  // couplings present
+    uint32_t R, Rcap;
+    int n_steps, method;
+    uint32_t k0, k1;         // Philox key = seed
+    uint32_t magicL, shiftL; // fast division by L
+    int nblk;                // blocks of the scan kernels
+    uint32_t* spins[2];
+    int32_t* E[2];
+    uint32_t* fam[2];
+    int32_t* M;
+    uint32_t* anc;
+    uint32_t* counts;
+    uint64_t* C;             // inclusive prefix of f (or of remainders, residual)
+    uint64_t* G;
+    uint32_t* hist;          // level histogram of the current population
+    uint64_t* flev;          // fixed-point tau-hat per level
+    double* tree;            // pairwise-sum scratch (power of two >= nlev)
+    uint64_t* partA;         // per-block partial sums
+    uint64_t* partB;
+    uint64_t* offA;          // per-block exclusive offsets
+    uint64_t* offB;
+    double* partD;
+    unsigned long long* partC2;
+    double* partCL;
+    const uint8_t* jbits;    // bit a of byte s: bond (s, s+e_a) has J = -1
+    const double* beta;      // n_steps + 1
+    const double* dbeta;     // n_steps
+    const double* q;         // exp(-4 dbeta), n_steps
+    const uint32_t* thr;     // 4 per step (index 1..d used)
+    const uint32_t* theta;   // n_steps
+    DevState* st;
+    TraceRow* trace;         // n_steps + 1 rows
+};
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
+
+}  // namespace pa
+
+// kernel launchers (defined in the .cu files)
+namespace pa {
+cudaError_t launch_init_spins(const KParams& p, cudaStream_t s);
+cudaError_t launch_measure(const KParams& p, int mode, int threads, cudaStream_t s);
+cudaError_t launch_resample(const KParams& p, cudaStream_t s, int64_t* launches);
+cudaError_t launch_sweep(const KParams& p, int threads, cudaStream_t s);
+cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int64_t* launches);
+int sweep_threads(int N);
+}  // namespace pa

@@ -1,0 +1,553 @@
+// pa_resample.cu -- reweighting, Q and copy counts (Sec. 2 step 2, Sec. 3),
+// the scan-plus-scatter that builds the ancestor array of the new population,
+// and the family / sampling-variance measurements (Eqs. rho_t, sv).
+//
+// All floating-point work uses explicitly rounded IEEE double operations
+// (no fused multiply-add) in a fixed order, so that the fixed-point weights
+// and therefore every count are reproducible bit for bit:
+//   level l = U >> 1 of a replica (U unsatisfied bonds), E = 2U - dN,
+//   w_k = q^k (q = exp(-4 dbeta), binary powering), k = l - l_min,
+//   S = fixed pairwise tree sum of n_k w_k over a power-of-two array,
+//   ln Q = (ln S - ln R_{i-1}) - dbeta E_min,
+//   f_k = floor(2^40 * ((R w_k) / S))  (tau-hat of Eq. taus in 2^-40 units).
+// The copy counts are exact integer functions of f and of Philox draws.
+#include <climits>
+
+#include "pa_internal.cuh"
+
+namespace pa {
+
+__device__ __forceinline__ double pow_bin(double q, uint32_t k) {
+    double r = 1.0, b = q;
+    while (k) {
+        if (k & 1u) r = __dmul_rn(r, b);
+        b = __dmul_rn(b, b);
+        k >>= 1;
+    }
+    return r;
+}
+
+// exp(x) = 2^n sum_{k<=13} r^k / k!, x = n ln2 + r (Cody-Waite reduction),
+// every operation explicitly rounded.  Used for the Poisson rule, x in [-16, 0].
+__device__ __forceinline__ double exp_taylor(double x) {
+    const double INV_LN2 = 0x1.71547652b82fep+0;
+    const double LN2_HI = 0x1.62e42fefa3800p-1;
+    const double LN2_LO = 0x1.ef35793c76730p-45;
+    const double c[14] = {0x1.0000000000000p+0,  0x1.0000000000000p+0,  0x1.0000000000000p-1,
+                          0x1.5555555555555p-3,  0x1.5555555555555p-5,  0x1.1111111111111p-7,
+                          0x1.6c16c16c16c17p-10, 0x1.a01a01a01a01ap-13, 0x1.a01a01a01a01ap-16,
+                          0x1.71de3a556c734p-19, 0x1.27e4fb7789f5cp-22, 0x1.ae64567f544e4p-26,
+                          0x1.1eed8eff8d898p-29, 0x1.6124613a86d09p-33};
+    const double nd = floor(__dadd_rn(__dmul_rn(x, INV_LN2), 0.5));
+    const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(nd, LN2_HI)), __dmul_rn(nd, LN2_LO));
+    double pp = c[13];
+#pragma unroll
+    for (int k = 12; k >= 0; --k) pp = __dadd_rn(__dmul_rn(pp, r), c[k]);
+    return scalbn(pp, (int)nd);
+}
+
+struct U128 {
+    uint64_t hi, lo;
+};
+__device__ __forceinline__ U128 mul128(uint64_t a, uint64_t b) { return {__umul64hi(a, b), a * b}; }
+__device__ __forceinline__ bool lt128(U128 a, U128 b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ bool le128(U128 a, U128 b) { return !lt128(b, a); }
+
+// Systematic rule: number of labels (k + u/2^32) T/R, k in [0,R), below x:
+// with xR = aT + b, that is a + [b 2^32 > u T], at most R.
+__device__ uint64_t sys_below(uint64_t x, uint64_t R, uint64_t T, uint32_t u) {
+    const U128 P = mul128(x, R);
+    uint64_t a = (uint64_t)(__ddiv_rn(__dmul_rn((double)x, (double)R), (double)T));
+    for (int it = 0; it < 8 && lt128(P, mul128(a, T)); ++it) --a;
+    for (int it = 0; it < 8 && le128(mul128(a + 1, T), P); ++it) ++a;
+    const uint64_t b = P.lo - a * T;  // < T, exact in the low 64 bits
+    const U128 lhs = {b >> 32, b << 32};
+    const U128 rhs = mul128((uint64_t)u, T);
+    const uint64_t n = a + (lt128(rhs, lhs) ? 1u : 0u);
+    return n < R ? n : R;
+}
+
+__device__ __forceinline__ int level_of(int32_t E, const KParams& p) {
+    return ((E + p.d * p.N) >> 1) >> 1;  // U = (E + dN)/2, level = U >> 1
+}
+
+// --------------------------------------------------------------------------
+// block helpers
+// --------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+// exclusive block scan of one value per thread (blockDim == SCAN_THREADS)
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T* sh, T* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T incl = warp_incl_scan(v, lane);
+    if (lane == 31) sh[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        T w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : (T)0;
+        T wi = warp_incl_scan(w, lane);
+        sh[lane] = wi - w;
+        if (lane == 31) sh[32] = wi;
+    }
+    __syncthreads();
+    T res = sh[warp] + incl - v;
+    *total = sh[32];
+    __syncthreads();
+    return res;
+}
+
+// --------------------------------------------------------------------------
+// K3: weights, S, ln Q, f table (one CTA)
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_weights(KParams p) {
+    DevState* st = p.st;
+    if (st->status != S_OK) return;
+    __shared__ int smin[32], smax[32];
+    const int i = st->step + 1;
+    const uint32_t Rprev = st->R_cur;
+    int lo = INT_MAX, hi = -1;
+    for (int l = threadIdx.x; l < p.nlev; l += blockDim.x)
+        if (p.hist[l]) {
+            lo = min(lo, l);
+            hi = max(hi, l);
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        smin[warp] = lo;
+        smax[warp] = hi;
+    }
+    __syncthreads();
+    lo = INT_MAX;
+    hi = -1;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        lo = min(lo, smin[w]);
+        hi = max(hi, smax[w]);
+    }
+    const int lmin = lo;
+    const int K = hi - lo + 1;
+    int P = 1;
+    while (P < K) P <<= 1;
+    const double q = p.q[i - 1];
+    volatile double* t = p.tree;
+    for (int k = threadIdx.x; k < P; k += blockDim.x)
+        t[k] = (k < K) ? __dmul_rn((double)p.hist[lmin + k], pow_bin(q, (uint32_t)k)) : 0.0;
+    __threadfence_block();
+    __syncthreads();
+    for (int h = P >> 1; h >= 1; h >>= 1) {
+        for (int k = threadIdx.x; k < h; k += blockDim.x) t[k] = __dadd_rn(t[k], t[k + h]);
+        __threadfence_block();
+        __syncthreads();
+    }
+    const double S = t[0];
+    const double Rd = (double)p.R;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double a = __dmul_rn(Rd, pow_bin(q, (uint32_t)k));
+        a = __ddiv_rn(a, S);
+        a = scalbn(a, FRAC_BITS);
+        p.flev[k] = (uint64_t)floor(a);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) p.hist[lmin + k] = 0u;
+    if (threadIdx.x == 0) {
+        const int32_t Umin = 2 * lmin + p.parity;
+        const int32_t Emin = 2 * Umin - p.d * p.N;
+        const double lnQ = __dsub_rn(__dsub_rn(log(S), log((double)Rprev)),
+                                     __dmul_rn(p.dbeta[i - 1], (double)Emin));
+        st->R_prev = Rprev;
+        st->lmin = (uint32_t)lmin;
+        st->K = (uint32_t)K;
+        st->sum_lnQ = __dadd_rn(st->sum_lnQ, lnQ);
+        TraceRow* tr = p.trace + i;
+        tr->lnQ = lnQ;
+        tr->sum_lnQ = st->sum_lnQ;
+        tr->c_ln_c = 0.0;
+        tr->sv_sum = 0.0;
+        tr->sumE = tr->sumE2 = tr->sumAbsM = tr->sumM2 = tr->sumC2 = tr->accepts = 0ull;
+        tr->R_prev = Rprev;
+        tr->R_i = 0;
+    }
+}
+
+// --------------------------------------------------------------------------
+// per-block sums of f (and of its 2^-40 fractional part)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t f_of(int j, const KParams& p, const int32_t* E, uint32_t lmin) {
+    return p.flev[level_of(E[j], p) - (int)lmin];
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_fsum(KParams p) {
+    const DevState* st = p.st;
+    if (st->status != S_OK) return;
+    __shared__ uint64_t sh[33];
+    const int i = st->step + 1;
+    const int32_t* E = p.E[(i - 1) & 1];
+    const uint32_t Rprev = st->R_prev, lmin = st->lmin;
+    const int j0 = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    uint64_t sf = 0, sg = 0;
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const int j = j0 + e;
+        if ((uint32_t)j < Rprev) {
+            const uint64_t f = f_of(j, p, E, lmin);
+            sf += f;
+            sg += f & ((1ull << FRAC_BITS) - 1);
+        }
+    }
+    uint64_t tot;
+    block_excl_scan(sf, sh, &tot);
+    if (threadIdx.x == 0) p.partA[blockIdx.x] = tot;
+    block_excl_scan(sg, sh, &tot);
+    if (threadIdx.x == 0) p.partB[blockIdx.x] = tot;
+}
+
+// exclusive scan of the per-block partials (one CTA of 1024 threads)
+__device__ void scan_partials(const uint64_t* part, uint64_t* off, int n, uint64_t* total_out) {
+    __shared__ uint64_t sh[33];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < n; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        const uint64_t v = (b < n) ? part[b] : 0ull;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        uint64_t incl = warp_incl_scan(v, lane);
+        if (lane == 31) sh[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint64_t w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0ull;
+            uint64_t wi = warp_incl_scan(w, lane);
+            sh[lane] = wi - w;
+            if (lane == 31) sh[32] = wi;
+        }
+        __syncthreads();
+        if (b < n) off[b] = carry + sh[warp] + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += sh[32];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void __launch_bounds__(1024) k_fscan(KParams p) {
+    DevState* st = p.st;
+    if (st->status != S_OK) return;
+    __shared__ uint64_t tA, tB;
+    scan_partials(p.partA, p.offA, p.nblk, &tA);
+    scan_partials(p.partB, p.offB, p.nblk, &tB);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->T = tA;
+        st->Tres = tB;
+        const uint64_t A = (tA - tB) >> FRAC_BITS;  // sum of floor(f / 2^40)
+        st->Rres = (uint64_t)p.R - A;
+    }
+}
+
+// --------------------------------------------------------------------------
+// prefix sums C (and G) and the copy counts of the rules that need no search
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(SCAN_THREADS) k_counts(KParams p) {
+    DevState* st = p.st;
+    if (st->status != S_OK) return;
+    __shared__ uint64_t sh[33];
+    const int i = st->step + 1;
+    const int32_t* E = p.E[(i - 1) & 1];
+    const uint32_t Rprev = st->R_prev, lmin = st->lmin;
+    const uint64_t T = st->T;
+    const int j0 = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    uint64_t f[SCAN_ITEMS];
+    uint64_t sf = 0, sg = 0;
+#pragma unroll
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const int j = j0 + e;
+        f[e] = ((uint32_t)j < Rprev) ? f_of(j, p, E, lmin) : 0ull;
+        sf += f[e];
+        sg += f[e] & ((1ull << FRAC_BITS) - 1);
+    }
+    uint64_t tot;
+    uint64_t cf = block_excl_scan(sf, sh, &tot) + p.offA[blockIdx.x];
+    uint64_t cg = block_excl_scan(sg, sh, &tot) + p.offB[blockIdx.x];
+    const int method = p.method;
+    uint32_t usys = 0;
+    if (method == M_SYSTEMATIC)
+        usys = philox(0u, DOM_RESAMPLE | RULE_SYSTEMATIC, (uint32_t)i, 0u, p.k0, p.k1).x;
+    bool kmax = false;
+#pragma unroll 1
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const int j = j0 + e;
+        if ((uint32_t)j >= Rprev) break;
+        const uint64_t prevC = cf;
+        cf += f[e];
+        cg += f[e] & ((1ull << FRAC_BITS) - 1);
+        p.C[j] = cf;
+        if (method == M_RESIDUAL) p.G[j] = cg;
+        uint32_t r = 0;
+        if (method == M_NEAREST) {
+            const uint4x x = philox((uint32_t)j, DOM_RESAMPLE | RULE_NEAREST, (uint32_t)i, 0u,
+                                    p.k0, p.k1);
+            const uint64_t u40 = (((uint64_t)x.y << 32) | x.x) >> 24;
+            r = (uint32_t)(f[e] >> FRAC_BITS) +
+                (u40 < (f[e] & ((1ull << FRAC_BITS) - 1)) ? 1u : 0u);
+        } else if (method == M_SYSTEMATIC) {
+            r = (uint32_t)(sys_below(cf, p.R, T, usys) - sys_below(prevC, p.R, T, usys));
+        } else if (method == M_RESIDUAL) {
+            r = (uint32_t)(f[e] >> FRAC_BITS);
+        } else if (method == M_POISSON) {
+            const double lam = scalbn((double)f[e], -FRAC_BITS);
+            const uint32_t M = (uint32_t)(f[e] >> 44) + 1u;
+            const double lc = __ddiv_rn(lam, (double)M);
+            uint32_t total = 0;
+            for (uint32_t m = 0; m < M; ++m) {
+                const uint4x x = philox((uint32_t)j, DOM_RESAMPLE | RULE_POISSON, (uint32_t)i, m,
+                                        p.k0, p.k1);
+                const double u = scalbn((double)((((uint64_t)x.y << 32) | x.x) >> 11), -53);
+                double pr = exp_taylor(-lc);
+                double Pc = pr;
+                uint32_t k = 0;
+                while (u >= Pc) {
+                    k += 1;
+                    if (k > POISSON_KMAX) {
+                        kmax = true;
+                        break;
+                    }
+                    pr = __ddiv_rn(__dmul_rn(pr, lc), (double)k);
+                    Pc = __dadd_rn(Pc, pr);
+                }
+                total += k;
+            }
+            r = total;
+        }
+        p.counts[j] = r;
+    }
+    if (kmax) atomicCAS(&st->status, S_OK, S_KMAX);
+}
+
+// multinomial draws (multinomial rule: R draws over C; residual rule: R_res
+// draws over the remainders G, or over C if every remainder is zero)
+__global__ void __launch_bounds__(256) k_draws(KParams p) {
+    const DevState* st = p.st;
+    if (st->status != S_OK) return;
+    const int i = st->step + 1;
+    const uint32_t Rprev = st->R_prev;
+    uint64_t n;
+    const uint64_t* box;
+    uint64_t total;
+    uint32_t rule;
+    if (p.method == M_MULTINOMIAL) {
+        n = p.R;
+        box = p.C;
+        total = st->T;
+        rule = RULE_MULTINOMIAL;
+    } else {
+        n = st->Rres;
+        const bool use_g = st->Tres > 0;
+        box = use_g ? p.G : p.C;
+        total = use_g ? st->Tres : st->T;
+        rule = RULE_RESIDUAL;
+    }
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4x x = philox((uint32_t)(k >> 1), DOM_RESAMPLE | rule, (uint32_t)i, 0u, p.k0,
+                                p.k1);
+        const uint64_t u = (k & 1) ? (((uint64_t)x.w << 32) | x.z) : (((uint64_t)x.y << 32) | x.x);
+        const uint64_t pos = __umul64hi(u, total);
+        uint32_t lo = 0, hi = Rprev;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (pos < box[mid]) hi = mid;
+            else lo = mid + 1;
+        }
+        atomicAdd(&p.counts[lo], 1u);
+    }
+}
+
+// --------------------------------------------------------------------------
+// scan of the counts and scatter of the ancestor array
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(SCAN_THREADS) k_rsum(KParams p) {
+    const DevState* st = p.st;
+    if (st->status != S_OK) return;
+    __shared__ uint64_t sh[33];
+    const uint32_t Rprev = st->R_prev;
+    const int j0 = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    uint64_t s = 0;
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const int j = j0 + e;
+        if ((uint32_t)j < Rprev) s += p.counts[j];
+    }
+    uint64_t tot;
+    block_excl_scan(s, sh, &tot);
+    if (threadIdx.x == 0) p.partA[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_rscan(KParams p) {
+    DevState* st = p.st;
+    if (st->status != S_OK) return;
+    __shared__ uint64_t tA;
+    scan_partials(p.partA, p.offA, p.nblk, &tA);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // a population that outgrows its capacity, or dies out, stops the run
+        if (tA > (uint64_t)p.Rcap || tA == 0) st->status = S_CAPACITY;
+        else st->R_cur = (uint32_t)tA;
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scatter(KParams p) {
+    const DevState* st = p.st;
+    if (st->status != S_OK) return;
+    __shared__ uint64_t sh[33];
+    __shared__ double sd[SCAN_THREADS];
+    const int i = st->step + 1;
+    const int32_t* E = p.E[(i - 1) & 1];
+    const uint32_t Rprev = st->R_prev, lmin = st->lmin;
+    const int j0 = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    uint32_t r[SCAN_ITEMS];
+    uint64_t s = 0;
+#pragma unroll
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const int j = j0 + e;
+        r[e] = ((uint32_t)j < Rprev) ? p.counts[j] : 0u;
+        s += r[e];
+    }
+    uint64_t tot;
+    uint64_t o = block_excl_scan(s, sh, &tot) + p.offA[blockIdx.x];
+    double sv = 0.0;
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const int j = j0 + e;
+        if ((uint32_t)j >= Rprev) break;
+        for (uint32_t c = 0; c < r[e]; ++c) p.anc[o + c] = (uint32_t)j;
+        o += r[e];
+        const double tau = scalbn((double)f_of(j, p, E, lmin), -FRAC_BITS);
+        const double dl = __dsub_rn((double)r[e], tau);
+        sv = __dadd_rn(sv, __dmul_rn(dl, dl));
+    }
+    // fixed-order tree reduction of the block's sampling-variance terms
+    sd[threadIdx.x] = sv;
+    __syncthreads();
+    for (int h = SCAN_THREADS / 2; h >= 1; h >>= 1) {
+        if ((int)threadIdx.x < h) sd[threadIdx.x] = __dadd_rn(sd[threadIdx.x], sd[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) p.partD[blockIdx.x] = sd[0];
+}
+
+// --------------------------------------------------------------------------
+// family statistics of the new population (families stay sorted by slot)
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
+    const DevState* st = p.st;
+    if (st->status != S_OK) return;
+    __shared__ double sd[SCAN_THREADS];
+    __shared__ unsigned long long sc2;
+    const int i = (mode == 0) ? st->step + 1 : st->step;
+    const uint32_t Ri = st->R_cur;
+    const uint32_t* fam = p.fam[i & 1];
+    if (threadIdx.x == 0) sc2 = 0ull;
+    __syncthreads();
+    const int j0 = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    double cl = 0.0;
+    unsigned long long c2 = 0;
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const uint32_t dslot = (uint32_t)(j0 + e);
+        if (dslot >= Ri) break;
+        const uint32_t f = fam[dslot];
+        if (dslot > 0 && fam[dslot - 1] == f) continue;
+        uint32_t lo = dslot + 1, hi = Ri;  // first index past the run of f
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (fam[mid] == f) lo = mid + 1;
+            else hi = mid;
+        }
+        const uint64_t c = lo - dslot;
+        c2 += c * c;
+        if (c > 1) cl = __dadd_rn(cl, __dmul_rn((double)c, log((double)c)));
+    }
+    for (int o = 16; o > 0; o >>= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    if ((threadIdx.x & 31) == 0 && c2) atomicAdd(&sc2, c2);
+    sd[threadIdx.x] = cl;
+    __syncthreads();
+    for (int h = SCAN_THREADS / 2; h >= 1; h >>= 1) {
+        if ((int)threadIdx.x < h) sd[threadIdx.x] = __dadd_rn(sd[threadIdx.x], sd[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        p.partCL[blockIdx.x] = sd[0];
+        if (sc2) atomicAdd(&p.trace[i].sumC2, sc2);
+    }
+}
+
+// fixed-order sums of the per-block partials, close the step
+__global__ void __launch_bounds__(256) k_finish(KParams p, int mode) {
+    DevState* st = p.st;
+    if (st->status != S_OK) return;
+    __shared__ double a[256], b[256];
+    const int i = (mode == 0) ? st->step + 1 : st->step;
+    const int nb_sv = (mode == 0) ? (int)((st->R_prev + SCAN_CHUNK - 1) / SCAN_CHUNK) : 0;
+    const int nb_f = (int)((st->R_cur + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    double sa = 0.0, sb = 0.0;
+    for (int k = threadIdx.x; k < nb_sv; k += blockDim.x) sa = __dadd_rn(sa, p.partD[k]);
+    for (int k = threadIdx.x; k < nb_f; k += blockDim.x) sb = __dadd_rn(sb, p.partCL[k]);
+    a[threadIdx.x] = sa;
+    b[threadIdx.x] = sb;
+    __syncthreads();
+    for (int h = 128; h >= 1; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            a[threadIdx.x] = __dadd_rn(a[threadIdx.x], a[threadIdx.x + h]);
+            b[threadIdx.x] = __dadd_rn(b[threadIdx.x], b[threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        TraceRow* tr = p.trace + i;
+        tr->sv_sum = a[0];
+        tr->c_ln_c = b[0];
+        tr->R_i = st->R_cur;
+        if (mode == 0) st->step = i;
+        else tr->R_prev = st->R_cur;
+    }
+}
+
+// --------------------------------------------------------------------------
+cudaError_t launch_resample(const KParams& p, cudaStream_t s, int64_t* launches) {
+    k_weights<<<1, 1024, 0, s>>>(p);
+    k_fsum<<<p.nblk, SCAN_THREADS, 0, s>>>(p);
+    k_fscan<<<1, 1024, 0, s>>>(p);
+    k_counts<<<p.nblk, SCAN_THREADS, 0, s>>>(p);
+    int n = 4;
+    if (p.method == M_MULTINOMIAL || p.method == M_RESIDUAL) {
+        int grid = (int)((p.R + 255u) / 256u);
+        if (grid > 4096) grid = 4096;
+        k_draws<<<grid, 256, 0, s>>>(p);
+        ++n;
+    }
+    k_rsum<<<p.nblk, SCAN_THREADS, 0, s>>>(p);
+    k_rscan<<<1, 1024, 0, s>>>(p);
+    k_scatter<<<p.nblk, SCAN_THREADS, 0, s>>>(p);
+    n += 3;
+    if (launches) *launches += n;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int64_t* launches) {
+    int nb = (int)((p.Rcap + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    k_family<<<nb, SCAN_THREADS, 0, s>>>(p, mode);
+    k_finish<<<1, 256, 0, s>>>(p, mode);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace pa

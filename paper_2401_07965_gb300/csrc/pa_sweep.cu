@@ -1,0 +1,430 @@
+// pa_sweep.cu -- initial population and the theta checkerboard Metropolis
+// sweeps of Sec. 2 step 3, fused with the replica copy of step 2 and the
+// measurements of step 4.
+//
+// Layout.  In HBM a replica is a row of Wp uint32 words (bit s&31 of word
+// s>>5 = site s; Wp = ceil(N/32) rounded up to 4 so rows are 16-byte
+// aligned).  A CTA owns 32 consecutive destination slots.  It reads the 32
+// parent rows named by the ancestor array (the gather of the resampling
+// step), transposes each 32x32 bit block with warp shuffles into one word per
+// site whose bit r is replica r ("multi-spin" layout), and keeps the whole
+// lattice of its 32 replicas in shared memory for all theta sweeps.  Neighbour
+// sums and acceptance masks are then bit-parallel over the 32 replicas; only
+// the uniform draw and its threshold compare are per (replica, site).
+//
+// Metropolis at beta_i: for site s with n unsatisfied bonds out of 2d,
+// dE = 4 (d - n).  dE <= 0 flips; dE = 4k > 0 flips iff u < thr[k], u the
+// uint32 draw of Philox counter (quad, (sweep<<1)|colour, step, slot) lane
+// k&3 where k = s >> 1 is the index of s among the sites of its colour.
+// Colour 0 (x+y+z even) is updated before colour 1 in every sweep.
+//
+// After the sweeps the CTA recomputes E = 2U - dN (U = unsatisfied bonds)
+// and M, writes the 32 rows back, adds each replica to the energy-level
+// histogram used by the next reweighting, and adds the population sums of
+// E, E^2, |M|, M^2 and the accepted flips to the step's trace row.
+#include "pa_internal.cuh"
+
+namespace pa {
+
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+    // lane i holds row i (bit c = element (i, c)); returns column `lane`
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const int j = 16 >> t;
+        const uint32_t m0 = masks[t];
+        uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? ((x & ~m0) | ((y >> j) & m0)) : ((x & m0) | ((y << j) & ~m0));
+    }
+    return x;
+}
+
+__device__ __forceinline__ int div_L(int s, const KParams& p) {
+    return (int)(((uint64_t)(uint32_t)s * p.magicL) >> p.shiftL);
+}
+
+// ---------------------------------------------------------------------------
+// Initial population (Sec. 2 step 1): every site an independent fair bit.
+// Thread (j, g) writes words 4g..4g+3 of replica j from one INIT draw.
+// ---------------------------------------------------------------------------
+__global__ void k_init_spins(KParams p) {
+    const uint32_t nq = (uint32_t)(p.Wp >> 2);
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t total = (uint64_t)p.R * nq;
+    if (tid >= total) return;
+    const uint32_t j = (uint32_t)(tid / nq);
+    const uint32_t g = (uint32_t)(tid - (uint64_t)j * nq);
+    uint4x x = philox(g, DOM_INIT, 0u, j, p.k0, p.k1);
+    uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int word = 4 * (int)g + m;
+        const int lo = 32 * word;
+        if (lo >= p.N) w[m] = 0u;
+        else if (p.N - lo < 32) w[m] &= (1u << (p.N - lo)) - 1u;
+    }
+    uint4* dst = reinterpret_cast<uint4*>(p.spins[0] + (size_t)j * p.Wp) + g;
+    *dst = make_uint4(w[0], w[1], w[2], w[3]);
+    if (g == 0) p.fam[0][j] = j;
+}
+
+// ---------------------------------------------------------------------------
+// One quad of same-colour sites for the 32 replicas of the CTA.
+// ---------------------------------------------------------------------------
+template <int D, bool EA>
+__device__ __forceinline__ uint32_t update_quad(uint32_t* ms, const uint8_t* jb, const KParams& p,
+                                                int q, int colour, uint32_t c1v, uint32_t step,
+                                                uint32_t base, uint32_t vmask,
+                                                const uint32_t (&thr)[4]) {
+    const int L = p.L, N = p.N;
+    const int LL = L * L;
+    int sites[4];
+    uint32_t G[4][D];  // G[m][k-1]: replica needs u < thr[k] to flip (thermometer)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int k = 4 * q + m;
+        const int s0 = 2 * k;
+        if (s0 >= N) {
+            sites[m] = -1;
+#pragma unroll
+            for (int a = 0; a < D; ++a) G[m][a] = 0xFFFFFFFFu;
+            continue;
+        }
+        int q1 = div_L(s0, p);
+        int x = s0 - q1 * L, y, z = 0;
+        if (D == 3) {
+            z = div_L(q1, p);
+            y = q1 - z * L;
+        } else {
+            y = q1;
+        }
+        const int off = ((y + z) & 1) != colour;
+        const int s = s0 + off;
+        x += off;
+        sites[m] = s;
+        const int xp = (x == L - 1) ? s - (L - 1) : s + 1;
+        const int xm = (x == 0) ? s + (L - 1) : s - 1;
+        const int yp = (y == L - 1) ? s - (L - 1) * L : s + L;
+        const int ym = (y == 0) ? s + (L - 1) * L : s - L;
+        const uint32_t w = ms[s];
+        uint32_t P0 = w ^ ms[xp], P1 = w ^ ms[xm], P2 = w ^ ms[yp], P3 = w ^ ms[ym];
+        uint32_t P4 = 0, P5 = 0;
+        int zp = 0, zm = 0;
+        if (D == 3) {
+            zp = (z == L - 1) ? s - (L - 1) * LL : s + LL;
+            zm = (z == 0) ? s + (L - 1) * LL : s - LL;
+            P4 = w ^ ms[zp];
+            P5 = w ^ ms[zm];
+        }
+        if (EA) {
+            const uint32_t js = jb[s];
+            P0 ^= 0u - (js & 1u);
+            P1 ^= 0u - (uint32_t)(jb[xm] & 1u);
+            P2 ^= 0u - ((js >> 1) & 1u);
+            P3 ^= 0u - (uint32_t)((jb[ym] >> 1) & 1u);
+            if (D == 3) {
+                P4 ^= 0u - ((js >> 2) & 1u);
+                P5 ^= 0u - (uint32_t)((jb[zm] >> 2) & 1u);
+            }
+        }
+        if (D == 2) {
+            // n <= 1 and n == 0 over the 4 unsatisfied-bond planes
+            const uint32_t two = (P0 & P1) | (P2 & P3) | ((P0 | P1) & (P2 | P3));
+            G[m][0] = ~two;                     // dE > 0 needs n <= 1
+            G[m][D - 1] = ~(P0 | P1 | P2 | P3); // n == 0 : dE = 8
+        } else {
+            // bit-sliced 6-input count n = n0 + 2 n1 + 4 n2
+            const uint32_t sa = P0 ^ P1 ^ P2, ca = (P0 & P1) | (P2 & (P0 ^ P1));
+            const uint32_t sb = P3 ^ P4 ^ P5, cb = (P3 & P4) | (P5 & (P3 ^ P4));
+            const uint32_t n0 = sa ^ sb, kc = sa & sb;
+            const uint32_t n1 = ca ^ cb ^ kc, n2 = (ca & cb) | (kc & (ca ^ cb));
+            G[m][0] = ~n2 & ~(n1 & n0);  // n <= 2
+            G[m][1] = ~n2 & ~n1;         // n <= 1
+            G[m][D - 1] = ~(n0 | n1 | n2);  // n == 0
+        }
+    }
+
+    // Philox4x32-10 with counter (q, c1v, step, base + r): the first rounds
+    // do not depend on r and are evaluated once.
+    const uint32_t c0 = (uint32_t)q;
+    uint32_t h0a = __umulhi(PHILOX_M0, c0), l0a = PHILOX_M0 * c0;
+    uint32_t h1a = __umulhi(PHILOX_M1, step), l1a = PHILOX_M1 * step;
+    const uint32_t A0 = h1a ^ c1v ^ p.k0;       // round 1 outputs
+    const uint32_t A1 = l1a;
+    const uint32_t A2x = h0a ^ p.k1 ^ base;     // A2 = A2x ^ r
+    const uint32_t A3 = l0a;
+    const uint32_t k0r1 = p.k0 + PHILOX_W0, k1r1 = p.k1 + PHILOX_W1;
+    const uint32_t h0b = __umulhi(PHILOX_M0, A0), l0b = PHILOX_M0 * A0;  // round 2, lane 0
+    const uint32_t B1k = A1 ^ k0r1;
+    const uint32_t B2 = h0b ^ A3 ^ k1r1;        // round 2 outputs that do not depend on r
+    const uint32_t B3 = l0b;
+    const uint32_t k0r2 = k0r1 + PHILOX_W0, k1r2 = k1r1 + PHILOX_W1;
+    const uint32_t h1c = __umulhi(PHILOX_M1, B2), l1c = PHILOX_M1 * B2;  // round 3, lane 2
+    const uint32_t C0k = h1c ^ k0r2;
+    const uint32_t C2k = B3 ^ k1r2;
+    const uint32_t C1 = l1c;
+
+    uint32_t T[4][D];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int a = 0; a < D; ++a) T[m][a] = 0u;
+
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        // round 2 (lane 2 depends on r)
+        const uint32_t A2 = A2x ^ (uint32_t)r;
+        const uint32_t h1b = __umulhi(PHILOX_M1, A2), l1b = PHILOX_M1 * A2;
+        const uint32_t B0 = h1b ^ B1k;
+        const uint32_t B1 = l1b;
+        // round 3 (lane 0 depends on r)
+        const uint32_t h0c = __umulhi(PHILOX_M0, B0), l0c = PHILOX_M0 * B0;
+        uint32_t x0 = C0k ^ B1;
+        uint32_t x1 = C1;
+        uint32_t x2 = h0c ^ C2k;
+        uint32_t x3 = l0c;
+        uint32_t k0 = k0r2 + PHILOX_W0, k1 = k1r2 + PHILOX_W1;
+#pragma unroll
+        for (int rr = 3; rr < 10; ++rr) {
+            const uint32_t hi0 = __umulhi(PHILOX_M0, x0), lo0 = PHILOX_M0 * x0;
+            const uint32_t hi1 = __umulhi(PHILOX_M1, x2), lo1 = PHILOX_M1 * x2;
+            x0 = hi1 ^ x1 ^ k0;
+            x1 = lo1;
+            x2 = hi0 ^ x3 ^ k1;
+            x3 = lo0;
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        const uint32_t u[4] = {x0, x1, x2, x3};
+        const uint32_t bit = 1u << r;
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                if (u[m] < thr[a + 1]) T[m][a] |= bit;
+    }
+
+    uint32_t acc = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (sites[m] < 0) continue;
+        uint32_t f = vmask;
+#pragma unroll
+        for (int a = 0; a < D; ++a) f &= ~G[m][a] | T[m][a];
+        ms[sites[m]] ^= f;
+        acc += __popc(f);
+    }
+    return acc;
+}
+
+// ---------------------------------------------------------------------------
+// mode 0: one temperature step's copy + sweeps + measurement (slots of the
+//         new population, parents from the ancestor array).
+// mode 1: measurement of the current population only (init / restore).
+// ---------------------------------------------------------------------------
+template <int D, bool EA>
+__global__ void __launch_bounds__(256) k_group(KParams p, int mode) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t* ms = smem;
+    uint8_t* jb = reinterpret_cast<uint8_t*>(smem + p.N);
+    __shared__ int32_t sU[32];
+    __shared__ int32_t sNup[32];
+    __shared__ unsigned long long sAcc;
+
+    const DevState* st = p.st;
+    if (st->status != S_OK) return;
+    const int i = (mode == 0) ? st->step + 1 : st->step;
+    const uint32_t R = st->R_cur;
+    const uint32_t base = blockIdx.x * 32u;
+    if (base >= R) return;
+    const uint32_t nval = min(32u, R - base);
+    const uint32_t vmask = (nval == 32u) ? 0xFFFFFFFFu : ((1u << nval) - 1u);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int N = p.N, W = p.W, Wp = p.Wp;
+    const uint32_t* src = p.spins[mode == 0 ? ((i - 1) & 1) : (i & 1)];
+    uint32_t* dst = p.spins[i & 1];
+
+    if (threadIdx.x < 32) {
+        sU[threadIdx.x] = 0;
+        sNup[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) sAcc = 0ull;
+
+    const bool valid = (uint32_t)lane < nval;
+    uint32_t my_src = base + lane;
+    if (mode == 0 && valid) my_src = p.anc[base + lane];
+    if (mode == 0 && warp == 0 && valid) p.fam[i & 1][base + lane] = p.fam[(i - 1) & 1][my_src];
+
+    // gather the 32 parent rows and transpose them into the multi-spin layout
+    for (int c4 = warp; 4 * c4 < W; c4 += nwarp) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (valid) v = reinterpret_cast<const uint4*>(src + (size_t)my_src * Wp)[c4];
+        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int b = 4 * c4 + k;
+            if (b < W) {
+                const uint32_t t = transpose32(w4[k], lane);
+                const int s = 32 * b + lane;
+                if (s < N) ms[s] = t;
+            }
+        }
+    }
+    if (EA)
+        for (int s = threadIdx.x; s < N; s += blockDim.x) jb[s] = p.jbits[s];
+    __syncthreads();
+
+    uint32_t acc = 0;
+    if (mode == 0) {
+        const uint32_t theta = p.theta[i - 1];
+        uint32_t thr[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) thr[k] = p.thr[4 * (i - 1) + k];
+        const int nq = (N / 2 + 3) / 4;
+        for (uint32_t t = 0; t < theta; ++t) {
+            for (int colour = 0; colour < 2; ++colour) {
+                const uint32_t c1v = DOM_SWEEP | (t << 1) | (uint32_t)colour;
+                for (int q = threadIdx.x; q < nq; q += blockDim.x)
+                    acc += update_quad<D, EA>(ms, jb, p, q, colour, c1v, (uint32_t)i, base, vmask,
+                                              thr);
+                __syncthreads();
+            }
+        }
+    }
+
+    // measurement: unsatisfied bonds U and up-count per replica, write back
+    int32_t U = 0, nup = 0;
+    for (int c4 = warp; 4 * c4 < Wp; c4 += nwarp) {
+        uint32_t out[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int b = 4 * c4 + k;
+            out[k] = 0u;
+            if (b < W) {  // warp-uniform
+                const int s = 32 * b + lane;
+                const bool in = s < N;
+                const uint32_t w = in ? ms[s] : 0u;
+                const uint32_t tw = transpose32(w, lane);
+                out[k] = tw;
+                nup += __popc(tw);
+                // unsatisfied-bond planes of the + bonds of s (0 past the last site)
+                uint32_t P0 = 0u, P1 = 0u, P2 = 0u;
+                if (in) {
+                    int q1 = div_L(s, p);
+                    int x = s - q1 * p.L, y, z = 0;
+                    if (D == 3) {
+                        z = div_L(q1, p);
+                        y = q1 - z * p.L;
+                    } else {
+                        y = q1;
+                    }
+                    const int L = p.L;
+                    const int xp = (x == L - 1) ? s - (L - 1) : s + 1;
+                    const int yp = (y == L - 1) ? s - (L - 1) * L : s + L;
+                    const uint32_t js = EA ? (uint32_t)jb[s] : 0u;
+                    P0 = w ^ ms[xp] ^ (0u - (js & 1u));
+                    P1 = w ^ ms[yp] ^ (0u - ((js >> 1) & 1u));
+                    if (D == 3) {
+                        const int zp = (z == L - 1) ? s - (L - 1) * L * L : s + L * L;
+                        P2 = w ^ ms[zp] ^ (0u - ((js >> 2) & 1u));
+                    }
+                }
+                // all lanes take part in the transposes
+                U += __popc(transpose32(P0, lane));
+                U += __popc(transpose32(P1, lane));
+                if (D == 3) U += __popc(transpose32(P2, lane));
+            }
+        }
+        if (valid)
+            reinterpret_cast<uint4*>(dst + (size_t)(base + lane) * Wp)[c4] =
+                make_uint4(out[0], out[1], out[2], out[3]);
+    }
+    atomicAdd(&sU[lane], U);
+    atomicAdd(&sNup[lane], nup);
+    // accepted flips of the CTA
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0 && acc) atomicAdd(&sAcc, (unsigned long long)acc);
+    __syncthreads();
+
+    if (warp == 0) {
+        long long e = 0, e2 = 0, am = 0, m2 = 0;
+        if (valid) {
+            const int32_t Uv = sU[lane];
+            const int32_t E = 2 * Uv - p.d * N;
+            const int32_t M = N - 2 * sNup[lane];
+            p.E[i & 1][base + lane] = E;
+            p.M[base + lane] = M;
+            atomicAdd(&p.hist[Uv >> 1], 1u);
+            e = E;
+            e2 = (long long)E * E;
+            am = M < 0 ? -M : M;
+            m2 = (long long)M * M;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+            e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+            am += __shfl_xor_sync(0xffffffffu, am, o);
+            m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+        }
+        if (lane == 0) {
+            TraceRow* tr = p.trace + i;
+            atomicAdd(&tr->sumE, (unsigned long long)e);
+            atomicAdd(&tr->sumE2, (unsigned long long)e2);
+            atomicAdd(&tr->sumAbsM, (unsigned long long)am);
+            atomicAdd(&tr->sumM2, (unsigned long long)m2);
+            if (sAcc) atomicAdd(&tr->accepts, sAcc);
+        }
+    }
+}
+
+int sweep_threads(int N) {
+    const int nq = (N / 2 + 3) / 4;
+    int t = ((nq + 31) / 32) * 32;
+    if (t < 32) t = 32;
+    if (t > 256) t = 256;
+    return t;
+}
+
+static size_t group_smem(const KParams& p) {
+    return (size_t)p.N * 4 + (p.ea ? (size_t)((p.N + 15) / 16) * 16 : 0);
+}
+
+template <int D, bool EA>
+static cudaError_t launch_group_t(const KParams& p, int mode, int threads, cudaStream_t s) {
+    const size_t smem = group_smem(p);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_group<D, EA>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const unsigned grid = (p.Rcap + 31u) / 32u;
+    k_group<D, EA><<<grid, threads, smem, s>>>(p, mode);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_group(const KParams& p, int mode, int threads, cudaStream_t s) {
+    if (p.d == 2) return p.ea ? launch_group_t<2, true>(p, mode, threads, s)
+                              : launch_group_t<2, false>(p, mode, threads, s);
+    return p.ea ? launch_group_t<3, true>(p, mode, threads, s)
+                : launch_group_t<3, false>(p, mode, threads, s);
+}
+
+cudaError_t launch_init_spins(const KParams& p, cudaStream_t s) {
+    const uint64_t total = (uint64_t)p.R * (uint64_t)(p.Wp / 4);
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    k_init_spins<<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_measure(const KParams& p, int mode, int threads, cudaStream_t s) {
+    return launch_group(p, mode, threads, s);
+}
+
+cudaError_t launch_sweep(const KParams& p, int threads, cudaStream_t s) {
+    return launch_group(p, 0, threads, s);
+}
+
+}  // namespace pa

@@ -1,0 +1,313 @@
+"""Thin Python binding of the C ABI in include/pa.h (argument marshalling only).
+
+Every function below has the name of the C entry point it calls; the work of a
+population-annealing step runs in the CUDA kernels of libpa.so.  PyTorch is
+used, when wanted, only to own the device workspace and to supply the stream.
+
+If libpa.so cannot be loaded this module raises at import time: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PA_OK, PA_ERR_ARG, PA_ERR_CUDA, PA_ERR_NOMEM, PA_ERR_CAPACITY = 0, 1, 2, 3, 4
+PA_ERR_POISSON_KMAX, PA_ERR_TIMEOUT, PA_ERR_STATE, PA_ERR_DONE = 5, 6, 7, 8
+
+PA_MULTINOMIAL, PA_SYSTEMATIC, PA_RESIDUAL, PA_POISSON, PA_NEAREST = 0, 1, 2, 3, 4
+RESAMPLERS = {"multinomial": 0, "systematic": 1, "residual": 2, "poisson": 3, "nearest": 4}
+
+PA_COUPLING_FERRO, PA_COUPLING_EA_PM, PA_COUPLING_EXPLICIT = 0, 1, 2
+PA_ARRAY_SPINS, PA_ARRAY_ENERGY, PA_ARRAY_FAMILY = 0, 1, 2
+PA_ARRAY_COUNTS, PA_ARRAY_ANCESTOR, PA_ARRAY_MAGNET = 3, 4, 5
+
+EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observables", "pa_trace",
+           "pa_free_energy", "pa_get_array", "pa_set_state", "pa_enable_timing",
+           "pa_sweep_timing", "pa_launch_count", "pa_destroy", "pa_strerror"]
+
+
+class pa_lattice(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("L", C.c_int32)]
+
+
+class pa_couplings(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("realization", C.c_uint32), ("disorder_seed", C.c_uint64),
+                ("J", C.POINTER(C.c_int8))]
+
+
+class pa_schedule(C.Structure):
+    _fields_ = [("n_steps", C.c_int32), ("beta", C.POINTER(C.c_double)),
+                ("theta", C.POINTER(C.c_uint32))]
+
+
+class pa_obs(C.Structure):
+    _fields_ = [("step", C.c_int32), ("R_i", C.c_uint32), ("R_prev", C.c_uint32),
+                ("pad0", C.c_uint32), ("beta", C.c_double), ("lnQ", C.c_double),
+                ("sum_lnQ", C.c_double), ("sumE", C.c_int64), ("sumE2", C.c_int64),
+                ("sumAbsM", C.c_int64), ("sumM2", C.c_int64), ("sumC2", C.c_int64),
+                ("accepts", C.c_uint64), ("entropy", C.c_double), ("sv", C.c_double),
+                ("e", C.c_double), ("e2", C.c_double), ("absm", C.c_double), ("m2", C.c_double),
+                ("c", C.c_double), ("chi", C.c_double), ("rho_t", C.c_double),
+                ("accept_rate", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad0"}
+
+
+class PAError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {pa_strerror(status)} (status {status})")
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libpa.so is not built ({path}); run __graft_entry__.build() first")
+    lib = C.CDLL(path)
+    vp, sz = C.c_void_p, C.c_size_t
+    lib.pa_workspace_bytes.argtypes = [C.POINTER(pa_lattice), C.c_uint32, C.c_uint32, C.c_int32,
+                                       C.c_int]
+    lib.pa_workspace_bytes.restype = sz
+    lib.pa_init.argtypes = [C.POINTER(vp), C.POINTER(pa_lattice), C.POINTER(pa_couplings),
+                            C.c_uint32, C.c_uint32, C.POINTER(pa_schedule), C.c_int, C.c_uint64,
+                            vp, vp, sz]
+    lib.pa_step.argtypes = [vp, C.c_int32]
+    lib.pa_sync.argtypes = [vp]
+    lib.pa_observables.argtypes = [vp, C.POINTER(pa_obs)]
+    lib.pa_trace.argtypes = [vp, C.POINTER(pa_obs), C.c_int32, C.POINTER(C.c_int32)]
+    lib.pa_free_energy.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.pa_get_array.argtypes = [vp, C.c_int, vp, sz, C.POINTER(sz)]
+    lib.pa_set_state.argtypes = [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32,
+                                 C.c_int32, C.c_double]
+    lib.pa_enable_timing.argtypes = [vp, C.c_int32]
+    lib.pa_sweep_timing.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_double)]
+    lib.pa_launch_count.argtypes = [vp]
+    lib.pa_launch_count.restype = C.c_int64
+    lib.pa_destroy.argtypes = [vp]
+    lib.pa_strerror.argtypes = [C.c_int]
+    lib.pa_strerror.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("pa_workspace_bytes", "pa_launch_count", "pa_strerror"):
+            getattr(lib, name).restype = C.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status, where):
+    if status != PA_OK:
+        raise PAError(status, where)
+
+
+def _lat(dim, L):
+    return pa_lattice(int(dim), int(L))
+
+
+# ---- the C entry points, one to one ---------------------------------------------------------
+
+def pa_strerror(status: int) -> str:
+    return _lib.pa_strerror(int(status)).decode()
+
+
+def pa_workspace_bytes(dim, L, R, R_cap, n_steps, resampler) -> int:
+    lat = _lat(dim, L)
+    return int(_lib.pa_workspace_bytes(C.byref(lat), R, R_cap, n_steps, int(resampler)))
+
+
+def pa_init(dim, L, couplings, R, R_cap, betas, thetas, resampler, seed, stream=0,
+            workspace=0, workspace_bytes=0):
+    """couplings: ('ferro',), ('ea', disorder_seed, realization) or ('explicit', J int8 array)."""
+    lat = _lat(dim, L)
+    keep = []
+    if couplings[0] == "ferro":
+        cpl = pa_couplings(PA_COUPLING_FERRO, 0, 0, None)
+    elif couplings[0] == "ea":
+        cpl = pa_couplings(PA_COUPLING_EA_PM, int(couplings[2]), int(couplings[1]), None)
+    elif couplings[0] == "explicit":
+        J = np.ascontiguousarray(couplings[1], np.int8)
+        keep.append(J)
+        cpl = pa_couplings(PA_COUPLING_EXPLICIT, 0, 0, J.ctypes.data_as(C.POINTER(C.c_int8)))
+    else:
+        raise ValueError(f"unknown couplings {couplings[0]!r}")
+    b = np.ascontiguousarray(betas, np.float64)
+    t = np.ascontiguousarray(thetas, np.uint32)
+    sch = pa_schedule(len(b) - 1, b.ctypes.data_as(C.POINTER(C.c_double)),
+                      t.ctypes.data_as(C.POINTER(C.c_uint32)))
+    ctx = C.c_void_p()
+    st = _lib.pa_init(C.byref(ctx), C.byref(lat), C.byref(cpl), int(R), int(R_cap), C.byref(sch),
+                      int(resampler), int(seed) & (2 ** 64 - 1), C.c_void_p(stream),
+                      C.c_void_p(workspace), int(workspace_bytes))
+    _check(st, "pa_init")
+    return ctx
+
+
+def pa_step(ctx, n=1):
+    _check(_lib.pa_step(ctx, int(n)), "pa_step")
+
+
+def pa_sync(ctx):
+    _check(_lib.pa_sync(ctx), "pa_sync")
+
+
+def pa_observables(ctx) -> dict:
+    o = pa_obs()
+    _check(_lib.pa_observables(ctx, C.byref(o)), "pa_observables")
+    return o.as_dict()
+
+
+def pa_trace(ctx, max_rows) -> list:
+    rows = (pa_obs * max_rows)()
+    n = C.c_int32()
+    _check(_lib.pa_trace(ctx, rows, max_rows, C.byref(n)), "pa_trace")
+    return [rows[i].as_dict() for i in range(n.value)]
+
+
+def pa_free_energy(ctx):
+    a, b = C.c_double(), C.c_double()
+    _check(_lib.pa_free_energy(ctx, C.byref(a), C.byref(b)), "pa_free_energy")
+    return a.value, b.value
+
+
+_ARRAY_DTYPE = {PA_ARRAY_SPINS: np.uint32, PA_ARRAY_ENERGY: np.int32, PA_ARRAY_FAMILY: np.uint32,
+                PA_ARRAY_COUNTS: np.uint32, PA_ARRAY_ANCESTOR: np.uint32,
+                PA_ARRAY_MAGNET: np.int32}
+
+
+def pa_get_array(ctx, which, capacity):
+    out = np.zeros(int(capacity), _ARRAY_DTYPE[which])
+    n = C.c_size_t()
+    _check(_lib.pa_get_array(ctx, int(which), out.ctypes.data_as(C.c_void_p), out.size,
+                             C.byref(n)), "pa_get_array")
+    return out[: n.value]
+
+
+def pa_set_state(ctx, spins_words, family, R_i, step, sum_lnQ):
+    s = np.ascontiguousarray(spins_words, np.uint32)
+    fam_p = None
+    if family is not None:
+        f = np.ascontiguousarray(family, np.uint32)
+        fam_p = f.ctypes.data_as(C.POINTER(C.c_uint32))
+    _check(_lib.pa_set_state(ctx, s.ctypes.data_as(C.POINTER(C.c_uint32)), fam_p, int(R_i),
+                             int(step), float(sum_lnQ)), "pa_set_state")
+
+
+def pa_enable_timing(ctx, on=True):
+    _check(_lib.pa_enable_timing(ctx, 1 if on else 0), "pa_enable_timing")
+
+
+def pa_sweep_timing(ctx):
+    ms, n, u = C.c_double(), C.c_int64(), C.c_double()
+    _check(_lib.pa_sweep_timing(ctx, C.byref(ms), C.byref(n), C.byref(u)), "pa_sweep_timing")
+    return ms.value, n.value, u.value
+
+
+def pa_launch_count(ctx) -> int:
+    return int(_lib.pa_launch_count(ctx))
+
+
+def pa_destroy(ctx):
+    _check(_lib.pa_destroy(ctx), "pa_destroy")
+
+
+# ---- a convenience owner of one run ---------------------------------------------------------
+
+class Population:
+    """One PA run: owns a context and, optionally, a torch-allocated workspace."""
+
+    def __init__(self, dim, L, R, betas, thetas, resampler="systematic", seed=1,
+                 couplings=("ferro",), R_cap=0, use_torch_memory=True, stream=None):
+        self.dim, self.L, self.N = dim, L, L ** dim
+        self.W = (self.N + 31) // 32
+        self.betas = np.ascontiguousarray(betas, np.float64)
+        self.thetas = np.ascontiguousarray(thetas, np.uint32)
+        self.n_steps = len(self.betas) - 1
+        self.resampler = RESAMPLERS[resampler] if isinstance(resampler, str) else int(resampler)
+        self.R = R
+        self.R_cap = R_cap if R_cap else default_capacity(R, self.resampler)
+        self._ws = None
+        ws_ptr, ws_bytes, stream_ptr = 0, 0, 0
+        if use_torch_memory:
+            import torch
+            nbytes = pa_workspace_bytes(dim, L, R, R_cap, self.n_steps, self.resampler)
+            if nbytes == 0:
+                raise PAError(PA_ERR_ARG, "pa_workspace_bytes")
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            ws_ptr = (self._ws.data_ptr() + 255) & ~255
+            ws_bytes = nbytes
+            s = stream if stream is not None else torch.cuda.current_stream()
+            stream_ptr = s.cuda_stream
+        elif stream is not None:
+            stream_ptr = stream.cuda_stream
+        self.ctx = pa_init(dim, L, couplings, R, R_cap, self.betas, self.thetas, self.resampler,
+                           seed, stream_ptr, ws_ptr, ws_bytes)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            pa_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        pa_step(self.ctx, n)
+
+    def observables(self):
+        return pa_observables(self.ctx)
+
+    def trace(self):
+        return pa_trace(self.ctx, self.n_steps + 1)
+
+    def free_energy(self):
+        return pa_free_energy(self.ctx)
+
+    @property
+    def size(self):
+        return self.observables()["R_i"]
+
+    def spins_words(self):
+        cap = self.R_cap * self.W
+        w = pa_get_array(self.ctx, PA_ARRAY_SPINS, cap)
+        return w.reshape(-1, self.W)
+
+    def spins(self):
+        """int8 sigma[R_i][N] unpacked from the device bits (bit 1 = -1)."""
+        w = self.spins_words()
+        bits = ((w[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(w.shape[0], -1)
+        return (1 - 2 * bits[:, : self.N].astype(np.int8)).astype(np.int8)
+
+    def array(self, which):
+        return pa_get_array(self.ctx, which, self.R_cap)
+
+    def energies(self):
+        return self.array(PA_ARRAY_ENERGY)
+
+    def families(self):
+        return self.array(PA_ARRAY_FAMILY)
+
+    def counts(self):
+        return self.array(PA_ARRAY_COUNTS)
+
+    def ancestors(self):
+        return self.array(PA_ARRAY_ANCESTOR)
+
+    def magnetisations(self):
+        return self.array(PA_ARRAY_MAGNET)
+
+
+def default_capacity(R, resampler):
+    if resampler in (PA_POISSON, PA_NEAREST, "poisson", "nearest"):
+        return R + int(math.ceil(10 * math.sqrt(R))) + 64
+    return R
