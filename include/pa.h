@@ -53,7 +53,8 @@ typedef enum {
     PA_ERR_POISSON_KMAX = 5,  /* a Poisson inversion exceeded 256 per chunk (p < 1e-300)*/
     PA_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                          */
     PA_ERR_STATE = 7,         /* the context holds an earlier device error              */
-    PA_ERR_DONE = 8           /* the schedule has no further temperature step           */
+    PA_ERR_DONE = 8,          /* the schedule has no further temperature step           */
+    PA_ERR_LIMIT = 9          /* a size exceeds the fixed limit of pa_weights_static    */
 } pa_status;
 
 /* Copy-count rules of Sec. 3.  Multinomial, systematic and residual keep
@@ -186,6 +187,41 @@ pa_status pa_sweep_timing(pa_ctx *ctx, double *ms, int64_t *launches, double *up
 
 /* Number of kernels this context has launched so far. */
 int64_t pa_launch_count(const pa_ctx *ctx);
+
+/* Reweighting of one temperature step without any device allocation.
+ *
+ * Some callers cannot call cudaMalloc: code embedded in a host framework that
+ * owns all device memory through its own pool (a stray allocation would break
+ * its accounting or exceed its budget), services that forbid allocation after
+ * start-up because an allocation can block or fail under load, and callers
+ * that want the weights of a population they already hold without creating a
+ * context and its workspace.  This entry point serves them: it needs only the
+ * caller's input and output buffers.  The paper has no counterpart; it is the
+ * weights stage of pa_step offered on its own.
+ *
+ * From the energies E[0..R_prev) (device, int32, each a valid energy of the
+ * dim-dimensional periodic L^dim lattice whose number of J = -1 bonds has the
+ * given parity), for the step dbeta = beta_i - beta_{i-1} > 0 it writes
+ *   *lnQ (device double)          ln Q_i of Eq. (Q), the same bits as pa_step,
+ *   f[0..R_prev) (device uint64)  floor(2^40 tau-hat_j), tau-hat of Eq. (taus)
+ *                                 with nominal size R,
+ * asynchronously on cuda_stream (NULL = legacy default stream).  If an energy
+ * lies outside the lattice's range, *lnQ is set to NaN and f is not written.
+ *
+ * Scratch: one statically allocated device array (about 1.3 MB) that every
+ * GPU loading the library holds until the process exits.  Every call shares
+ * it and it keeps the last call's contents (the call clears what must start
+ * at zero), so calls whose kernels overlap on the GPU -- on different streams,
+ * or from several host threads -- race and must be serialised by the caller.
+ * The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture begins.
+ *
+ * Limits: dim*N/2 + 1 <= 65536 energy levels and N <= 32768 sites, else
+ * PA_ERR_LIMIT; other bad arguments give PA_ERR_ARG.  No cudaMalloc, cudaFree
+ * or allocating library routine is called. */
+pa_status pa_weights_static(const int32_t *E, uint32_t R_prev, uint32_t R, int32_t dim, int32_t L,
+                            int32_t parity, double dbeta, double *lnQ, uint64_t *f,
+                            void *cuda_stream);
 
 /* Release the context (and the device memory it allocated).  NULL is a no-op. */
 pa_status pa_destroy(pa_ctx *ctx);

@@ -1,6 +1,6 @@
 """Build the CUDA library libpa.so in-tree for sm_103a (nvcc, no CMake).
 
-The three translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 paper_2401_07965_gb300/lib/libpa.so.  The build is skipped when the library is
 newer than every source file.
 """
@@ -18,7 +18,7 @@ LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libpa.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["pa_sweep.cu", "pa_resample.cu", "pa_api.cu"]
+SOURCES = ["pa_sweep.cu", "pa_resample.cu", "pa_api.cu", "pa_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
           "-ffp-contract=off", "-fmad=false", "-I", INCLUDE, "-I", CSRC]

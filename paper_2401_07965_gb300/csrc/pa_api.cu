@@ -592,6 +592,7 @@ const char* pa_strerror(pa_status s) {
         case PA_ERR_TIMEOUT: return "a bounded device wait timed out";
         case PA_ERR_STATE: return "context holds an earlier error";
         case PA_ERR_DONE: return "schedule exhausted";
+        case PA_ERR_LIMIT: return "size exceeds the static scratch limit of pa_weights_static";
         default: return "unknown status";
     }
 }

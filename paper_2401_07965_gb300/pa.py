@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 PA_OK, PA_ERR_ARG, PA_ERR_CUDA, PA_ERR_NOMEM, PA_ERR_CAPACITY = 0, 1, 2, 3, 4
-PA_ERR_POISSON_KMAX, PA_ERR_TIMEOUT, PA_ERR_STATE, PA_ERR_DONE = 5, 6, 7, 8
+PA_ERR_POISSON_KMAX, PA_ERR_TIMEOUT, PA_ERR_STATE, PA_ERR_DONE, PA_ERR_LIMIT = 5, 6, 7, 8, 9
 
 PA_MULTINOMIAL, PA_SYSTEMATIC, PA_RESIDUAL, PA_POISSON, PA_NEAREST = 0, 1, 2, 3, 4
 RESAMPLERS = {"multinomial": 0, "systematic": 1, "residual": 2, "poisson": 3, "nearest": 4}
@@ -29,7 +29,8 @@ PA_ARRAY_COUNTS, PA_ARRAY_ANCESTOR, PA_ARRAY_MAGNET = 3, 4, 5
 
 EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observables", "pa_trace",
            "pa_free_energy", "pa_get_array", "pa_set_state", "pa_enable_timing",
-           "pa_sweep_timing", "pa_launch_count", "pa_destroy", "pa_strerror"]
+           "pa_sweep_timing", "pa_launch_count", "pa_destroy", "pa_strerror",
+           "pa_weights_static"]
 
 
 class pa_lattice(C.Structure):
@@ -92,6 +93,8 @@ def _load():
     lib.pa_launch_count.argtypes = [vp]
     lib.pa_launch_count.restype = C.c_int64
     lib.pa_destroy.argtypes = [vp]
+    lib.pa_weights_static.argtypes = [vp, C.c_uint32, C.c_uint32, C.c_int32, C.c_int32,
+                                      C.c_int32, C.c_double, vp, vp, vp]
     lib.pa_strerror.argtypes = [C.c_int]
     lib.pa_strerror.restype = C.c_char_p
     for name in EXPORTS:
@@ -212,6 +215,13 @@ def pa_sweep_timing(ctx):
 
 def pa_launch_count(ctx) -> int:
     return int(_lib.pa_launch_count(ctx))
+
+
+def pa_weights_static(E_ptr, R_prev, R, dim, L, parity, dbeta, lnQ_ptr, f_ptr, stream=0):
+    """Device pointers in, device pointers out; allocates nothing (see include/pa.h)."""
+    _check(_lib.pa_weights_static(C.c_void_p(E_ptr), int(R_prev), int(R), int(dim), int(L),
+                                  int(parity), float(dbeta), C.c_void_p(lnQ_ptr),
+                                  C.c_void_p(f_ptr), C.c_void_p(stream)), "pa_weights_static")
 
 
 def pa_destroy(ctx):
