@@ -209,8 +209,13 @@ def run_ours(args):
     seed = SEED + 1000 * rank
     stream = torch.cuda.current_stream(dev)
 
+    # launch configuration of the sweep from the autotuner (timed on this GPU, cached)
+    from paper_2401_07965_gb300 import tune
+    threads = tune.best_sweep_threads(DIM, L, R, theta=THETA, stream=stream)
+
     # warm-up on a throw-away run of the same shape
-    wu = pa.Population(DIM, L, R, betas, thetas, "systematic", seed + 99, stream=stream)
+    wu = pa.Population(DIM, L, R, betas, thetas, "systematic", seed + 99, stream=stream,
+                       sweep_threads=threads)
     wu.step(max(args.warmup, 1))
     wu.observables()
     wu.close()
@@ -227,7 +232,8 @@ def run_ours(args):
         remaining -= n
         r += 1
     for rule, n in plan:
-        runs.append(pa.Population(DIM, L, R, betas, thetas, rule, seed, stream=stream))
+        runs.append(pa.Population(DIM, L, R, betas, thetas, rule, seed, stream=stream,
+                                  sweep_threads=threads))
     for p in runs:
         pa.pa_enable_timing(p.ctx, True)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -274,7 +280,7 @@ def run_ours(args):
     del flush
 
     # end to end through the C ABI from host inputs to host results
-    e2e = run_e2e(args, pa, stream, seed, dev)
+    e2e = None if args.no_e2e else run_e2e(args, pa, stream, seed, dev, threads)
 
     if rank != 0:
         if world > 1:
@@ -310,6 +316,7 @@ def run_ours(args):
             "data": "synthetic (initial population drawn by the method at beta=0)",
             "config": {"workload": WORKLOAD, "rules": [r for r, _ in plan],
                        "l2": "flushed between steps (256 MiB write, outside the step events)",
+                       "sweep_threads": threads,
                        "parallelism": f"{world} independent runs" if world > 1 else "1 run"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches}
@@ -319,7 +326,28 @@ def run_ours(args):
     return 0
 
 
-def run_e2e(args, pa, stream, seed, dev):
+def run_small(args):
+    """Profiling case: one run of R=20000 replicas of the benchmark lattice, systematic
+    rule; W warm-up steps then K steps, all on one context."""
+    import torch
+    from paper_2401_07965_gb300 import pa
+    betas = np.linspace(0.0, BETA_F, NSTEPS + 1)
+    thetas = np.full(NSTEPS, THETA, np.uint32)
+    stream = torch.cuda.current_stream()
+    p = pa.Population(DIM, L, 20000, betas, thetas, "systematic", SEED, stream=stream,
+                      sweep_threads=args.threads)
+    p.step(args.warmup)
+    pa.pa_enable_timing(p.ctx, True)
+    p.step(args.steps)
+    ms, n, u = pa.pa_sweep_timing(p.ctx)
+    print(json.dumps({"case": "small", "R": 20000, "threads": pa.pa_get_sweep_threads(p.ctx),
+                      "sweep_ms_per_launch": ms / max(n, 1),
+                      "sweep_updates_per_ns": u / (ms * 1e6)}), flush=True)
+    p.close()
+    return 0
+
+
+def run_e2e(args, pa, stream, seed, dev, threads=0):
     """Whole runs through the C ABI: host schedule -> pa_init -> per step pa_step +
     pa_observables (device -> host) -> pa_free_energy.  Host wall clock."""
     import ctypes as C
@@ -339,6 +367,8 @@ def run_e2e(args, pa, stream, seed, dev):
         n = min(NSTEPS, n_total - done)
         ctx = pa.pa_init(DIM, L, ("ferro",), R, 0, betas, thetas, pa.RESAMPLERS[rule], seed,
                          stream.cuda_stream)
+        if threads:
+            pa.pa_set_sweep_threads(ctx, threads)
         h2d += betas.nbytes + thetas.nbytes + 3 * 8 * NSTEPS + 16 * NSTEPS
         for _ in range(n):
             pa.pa_step(ctx, 1)
@@ -363,11 +393,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--threads", type=int, default=0, help="small case: sweep threads per CTA")
+    ap.add_argument("--case", default="full", choices=["full", "small"],
+                    help="small: one run of R=20000 replicas of the same lattice (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "small":
+        return run_small(args)
     return run_ours(args)
 
 

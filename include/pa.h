@@ -28,7 +28,7 @@
  *  - Work is enqueued on the caller's CUDA stream (NULL = legacy default).
  *    pa_step is asynchronous.  A context must not be used from two host
  *    threads at once.
- *  - Lattice: dim in {2,3}, L even, 2 <= L, N = L^dim <= 2^20 sites,
+ *  - Lattice: dim in {2,3}, L even, 2 <= L, N = L^dim <= 32768 sites,
  *    periodic; site s = x + L*y (+ L*L*z).  Spins are stored one bit per
  *    site, bit (s & 31) of word (s >> 5), bit value 1 meaning sigma = -1.
  */
@@ -187,6 +187,13 @@ pa_status pa_sweep_timing(pa_ctx *ctx, double *ms, int64_t *launches, double *up
 
 /* Number of kernels this context has launched so far. */
 int64_t pa_launch_count(const pa_ctx *ctx);
+
+/* Launch configuration of the sweep kernel: threads per CTA (64, 128, 256 or
+ * 512; each CTA holds 32 replicas).  Results do not depend on it, only the
+ * speed; the package's autotuner times the candidates and picks one.
+ * PA_ERR_ARG for other values. */
+pa_status pa_set_sweep_threads(pa_ctx *ctx, int32_t threads);
+int32_t pa_get_sweep_threads(const pa_ctx *ctx);
 
 /* Reweighting of one temperature step without any device allocation.
  *

@@ -297,6 +297,10 @@ pa_status pa_init(pa_ctx** out, const pa_lattice* lat, const pa_couplings* cpl, 
     p.method = (int)resampler;
     p.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
     p.k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        p.rk0[r] = p.k0 + (uint32_t)r * PHILOX_W0;
+        p.rk1[r] = p.k1 + (uint32_t)r * PHILOX_W1;
+    }
     if (!make_magic(m.L, m.N, &p.magicL, &p.shiftL)) {
         pa_destroy(ctx);
         return PA_ERR_ARG;
@@ -569,6 +573,14 @@ pa_status pa_sweep_timing(pa_ctx* ctx, double* ms, int64_t* launches, double* up
 }
 
 int64_t pa_launch_count(const pa_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+pa_status pa_set_sweep_threads(pa_ctx* ctx, int32_t threads) {
+    if (!ctx || !sweep_threads_supported(threads)) return PA_ERR_ARG;
+    ctx->threads = threads;
+    return PA_OK;
+}
+
+int32_t pa_get_sweep_threads(const pa_ctx* ctx) { return ctx ? ctx->threads : 0; }
 
 pa_status pa_destroy(pa_ctx* ctx) {
     if (!ctx) return PA_OK;

@@ -56,6 +56,13 @@ __host__ __device__ __forceinline__ uint4x philox(uint32_t c0, uint32_t c1, uint
     return {c0, c1, c2, c3};
 }
 
+// 32x32 -> 64-bit product as one wide multiply
+__device__ __forceinline__ void mulhilo(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+    const uint64_t p = (uint64_t)a * (uint64_t)b;
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+}
+
 // Device state shared by the kernels of a run (one per context).
 struct DevState {
     int32_t step;      // completed temperature steps
@@ -91,6 +98,7 @@ struct KParams {
     uint32_t R, Rcap;
     int n_steps, method;
     uint32_t k0, k1;         // Philox key = seed
+    uint32_t rk0[10], rk1[10];  // its round keys k + r*W (round r = 0..9)
     uint32_t magicL, shiftL; // fast division by L
     int nblk;                // blocks of the scan kernels
     uint32_t* spins[2];
@@ -135,4 +143,5 @@ cudaError_t launch_resample(const KParams& p, cudaStream_t s, int64_t* launches)
 cudaError_t launch_sweep(const KParams& p, int threads, cudaStream_t s);
 cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int64_t* launches);
 int sweep_threads(int N);
+bool sweep_threads_supported(int t);
 }  // namespace pa

@@ -145,23 +145,25 @@ __device__ __forceinline__ uint32_t update_quad(uint32_t* ms, const uint8_t* jb,
     }
 
     // Philox4x32-10 with counter (q, c1v, step, base + r): the first rounds
-    // do not depend on r and are evaluated once.
+    // do not depend on r and are evaluated once; the round keys come from the
+    // kernel parameters.
     const uint32_t c0 = (uint32_t)q;
-    uint32_t h0a = __umulhi(PHILOX_M0, c0), l0a = PHILOX_M0 * c0;
-    uint32_t h1a = __umulhi(PHILOX_M1, step), l1a = PHILOX_M1 * step;
-    const uint32_t A0 = h1a ^ c1v ^ p.k0;       // round 1 outputs
+    uint32_t h0a, l0a, h1a, l1a;
+    mulhilo(PHILOX_M0, c0, h0a, l0a);
+    mulhilo(PHILOX_M1, step, h1a, l1a);
+    const uint32_t A0 = h1a ^ c1v ^ p.rk0[0];   // round 1 outputs
     const uint32_t A1 = l1a;
-    const uint32_t A2x = h0a ^ p.k1 ^ base;     // A2 = A2x ^ r
+    const uint32_t A2x = h0a ^ p.rk1[0] ^ base; // A2 = A2x ^ r
     const uint32_t A3 = l0a;
-    const uint32_t k0r1 = p.k0 + PHILOX_W0, k1r1 = p.k1 + PHILOX_W1;
-    const uint32_t h0b = __umulhi(PHILOX_M0, A0), l0b = PHILOX_M0 * A0;  // round 2, lane 0
-    const uint32_t B1k = A1 ^ k0r1;
-    const uint32_t B2 = h0b ^ A3 ^ k1r1;        // round 2 outputs that do not depend on r
+    uint32_t h0b, l0b;
+    mulhilo(PHILOX_M0, A0, h0b, l0b);           // round 2, lane 0
+    const uint32_t B1k = A1 ^ p.rk0[1];
+    const uint32_t B2 = h0b ^ A3 ^ p.rk1[1];    // round 2 outputs that do not depend on r
     const uint32_t B3 = l0b;
-    const uint32_t k0r2 = k0r1 + PHILOX_W0, k1r2 = k1r1 + PHILOX_W1;
-    const uint32_t h1c = __umulhi(PHILOX_M1, B2), l1c = PHILOX_M1 * B2;  // round 3, lane 2
-    const uint32_t C0k = h1c ^ k0r2;
-    const uint32_t C2k = B3 ^ k1r2;
+    uint32_t h1c, l1c;
+    mulhilo(PHILOX_M1, B2, h1c, l1c);           // round 3, lane 2
+    const uint32_t C0k = h1c ^ p.rk0[2];
+    const uint32_t C2k = B3 ^ p.rk1[2];
     const uint32_t C1 = l1c;
 
     uint32_t T[4][D];
@@ -174,26 +176,26 @@ __device__ __forceinline__ uint32_t update_quad(uint32_t* ms, const uint8_t* jb,
     for (int r = 0; r < 32; ++r) {
         // round 2 (lane 2 depends on r)
         const uint32_t A2 = A2x ^ (uint32_t)r;
-        const uint32_t h1b = __umulhi(PHILOX_M1, A2), l1b = PHILOX_M1 * A2;
+        uint32_t h1b, l1b;
+        mulhilo(PHILOX_M1, A2, h1b, l1b);
         const uint32_t B0 = h1b ^ B1k;
         const uint32_t B1 = l1b;
         // round 3 (lane 0 depends on r)
-        const uint32_t h0c = __umulhi(PHILOX_M0, B0), l0c = PHILOX_M0 * B0;
+        uint32_t h0c, l0c;
+        mulhilo(PHILOX_M0, B0, h0c, l0c);
         uint32_t x0 = C0k ^ B1;
         uint32_t x1 = C1;
         uint32_t x2 = h0c ^ C2k;
         uint32_t x3 = l0c;
-        uint32_t k0 = k0r2 + PHILOX_W0, k1 = k1r2 + PHILOX_W1;
 #pragma unroll
         for (int rr = 3; rr < 10; ++rr) {
-            const uint32_t hi0 = __umulhi(PHILOX_M0, x0), lo0 = PHILOX_M0 * x0;
-            const uint32_t hi1 = __umulhi(PHILOX_M1, x2), lo1 = PHILOX_M1 * x2;
-            x0 = hi1 ^ x1 ^ k0;
+            uint32_t hi0, lo0, hi1, lo1;
+            mulhilo(PHILOX_M0, x0, hi0, lo0);
+            mulhilo(PHILOX_M1, x2, hi1, lo1);
+            x0 = hi1 ^ x1 ^ p.rk0[rr];
             x1 = lo1;
-            x2 = hi0 ^ x3 ^ k1;
+            x2 = hi0 ^ x3 ^ p.rk1[rr];
             x3 = lo0;
-            k0 += PHILOX_W0;
-            k1 += PHILOX_W1;
         }
         const uint32_t u[4] = {x0, x1, x2, x3};
         const uint32_t bit = 1u << r;
@@ -222,8 +224,8 @@ __device__ __forceinline__ uint32_t update_quad(uint32_t* ms, const uint8_t* jb,
 //         new population, parents from the ancestor array).
 // mode 1: measurement of the current population only (init / restore).
 // ---------------------------------------------------------------------------
-template <int D, bool EA>
-__global__ void __launch_bounds__(256) k_group(KParams p, int mode) {
+template <int D, bool EA, int NT>
+__global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t* ms = smem;
     uint8_t* jb = reinterpret_cast<uint8_t*>(smem + p.N);
@@ -379,30 +381,41 @@ __global__ void __launch_bounds__(256) k_group(KParams p, int mode) {
 
 int sweep_threads(int N) {
     const int nq = (N / 2 + 3) / 4;
-    int t = ((nq + 31) / 32) * 32;
-    if (t < 32) t = 32;
-    if (t > 256) t = 256;
+    int t = 64;
+    while (t < nq && t < 256) t <<= 1;
     return t;
 }
+
+bool sweep_threads_supported(int t) { return t == 64 || t == 128 || t == 256 || t == 512; }
 
 static size_t group_smem(const KParams& p) {
     return (size_t)p.N * 4 + (p.ea ? (size_t)((p.N + 15) / 16) * 16 : 0);
 }
 
-template <int D, bool EA>
-static cudaError_t launch_group_t(const KParams& p, int mode, int threads, cudaStream_t s) {
+template <int D, bool EA, int NT>
+static cudaError_t launch_group_nt(const KParams& p, int mode, cudaStream_t s) {
     const size_t smem = group_smem(p);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_group<D, EA>,
+        cudaError_t e = cudaFuncSetAttribute(k_group<D, EA, NT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const unsigned grid = (p.Rcap + 31u) / 32u;
-    k_group<D, EA><<<grid, threads, smem, s>>>(p, mode);
+    k_group<D, EA, NT><<<grid, NT, smem, s>>>(p, mode);
     return cudaGetLastError();
+}
+
+template <int D, bool EA>
+static cudaError_t launch_group_t(const KParams& p, int mode, int threads, cudaStream_t s) {
+    switch (threads) {
+        case 64: return launch_group_nt<D, EA, 64>(p, mode, s);
+        case 128: return launch_group_nt<D, EA, 128>(p, mode, s);
+        case 512: return launch_group_nt<D, EA, 512>(p, mode, s);
+        default: return launch_group_nt<D, EA, 256>(p, mode, s);
+    }
 }
 
 static cudaError_t launch_group(const KParams& p, int mode, int threads, cudaStream_t s) {

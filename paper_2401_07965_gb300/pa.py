@@ -30,7 +30,7 @@ PA_ARRAY_COUNTS, PA_ARRAY_ANCESTOR, PA_ARRAY_MAGNET = 3, 4, 5
 EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observables", "pa_trace",
            "pa_free_energy", "pa_get_array", "pa_set_state", "pa_enable_timing",
            "pa_sweep_timing", "pa_launch_count", "pa_destroy", "pa_strerror",
-           "pa_weights_static"]
+           "pa_weights_static", "pa_set_sweep_threads", "pa_get_sweep_threads"]
 
 
 class pa_lattice(C.Structure):
@@ -95,10 +95,14 @@ def _load():
     lib.pa_destroy.argtypes = [vp]
     lib.pa_weights_static.argtypes = [vp, C.c_uint32, C.c_uint32, C.c_int32, C.c_int32,
                                       C.c_int32, C.c_double, vp, vp, vp]
+    lib.pa_set_sweep_threads.argtypes = [vp, C.c_int32]
+    lib.pa_get_sweep_threads.argtypes = [vp]
+    lib.pa_get_sweep_threads.restype = C.c_int32
     lib.pa_strerror.argtypes = [C.c_int]
     lib.pa_strerror.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("pa_workspace_bytes", "pa_launch_count", "pa_strerror"):
+        if name not in ("pa_workspace_bytes", "pa_launch_count", "pa_strerror",
+                        "pa_get_sweep_threads"):
             getattr(lib, name).restype = C.c_int
     return lib
 
@@ -224,6 +228,14 @@ def pa_weights_static(E_ptr, R_prev, R, dim, L, parity, dbeta, lnQ_ptr, f_ptr, s
                                   C.c_void_p(f_ptr), C.c_void_p(stream)), "pa_weights_static")
 
 
+def pa_set_sweep_threads(ctx, threads):
+    _check(_lib.pa_set_sweep_threads(ctx, int(threads)), "pa_set_sweep_threads")
+
+
+def pa_get_sweep_threads(ctx) -> int:
+    return int(_lib.pa_get_sweep_threads(ctx))
+
+
 def pa_destroy(ctx):
     _check(_lib.pa_destroy(ctx), "pa_destroy")
 
@@ -234,7 +246,8 @@ class Population:
     """One PA run: owns a context and, optionally, a torch-allocated workspace."""
 
     def __init__(self, dim, L, R, betas, thetas, resampler="systematic", seed=1,
-                 couplings=("ferro",), R_cap=0, use_torch_memory=True, stream=None):
+                 couplings=("ferro",), R_cap=0, use_torch_memory=True, stream=None,
+                 sweep_threads=None):
         self.dim, self.L, self.N = dim, L, L ** dim
         self.W = (self.N + 31) // 32
         self.betas = np.ascontiguousarray(betas, np.float64)
@@ -259,6 +272,8 @@ class Population:
             stream_ptr = stream.cuda_stream
         self.ctx = pa_init(dim, L, couplings, R, R_cap, self.betas, self.thetas, self.resampler,
                            seed, stream_ptr, ws_ptr, ws_bytes)
+        if sweep_threads:
+            pa_set_sweep_threads(self.ctx, sweep_threads)
 
     def close(self):
         if getattr(self, "ctx", None) is not None:

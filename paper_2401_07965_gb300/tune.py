@@ -1,0 +1,82 @@
+"""Autotuner for the launch configuration of the sweep kernel.
+
+The sweep kernel runs one CTA per 32 replicas; how many threads share a CTA
+(64-512) trades per-CTA parallelism against the number of CTAs resident per
+SM and the rounding of the grid into waves, which depends on the lattice and
+on the population size.  The tuner times each candidate on a throw-away run of
+the same shape (same lattice, couplings kind, R and theta; results never
+depend on the choice) and remembers the fastest per device and shape, in
+memory and in a small JSON cache file.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+from . import pa
+
+CANDIDATES = (64, 128, 256, 512)
+_CACHE = {}
+_CACHE_FILE = os.path.join(os.path.expanduser("~"), ".cache", "pa_gb300_tune.json")
+
+
+def _key(dim, L, R, ea, theta):
+    try:
+        import torch
+        dev = torch.cuda.get_device_name()
+    except Exception:
+        dev = "cuda"
+    return f"{dev}|d{dim}|L{L}|R{R}|ea{int(ea)}|theta{theta}"
+
+
+def _load():
+    if _CACHE:
+        return
+    try:
+        with open(_CACHE_FILE) as fh:
+            _CACHE.update(json.load(fh))
+    except Exception:
+        pass
+
+
+def _save():
+    try:
+        os.makedirs(os.path.dirname(_CACHE_FILE), exist_ok=True)
+        with open(_CACHE_FILE, "w") as fh:
+            json.dump(_CACHE, fh)
+    except Exception:
+        pass
+
+
+def best_sweep_threads(dim, L, R, couplings=("ferro",), theta=10, candidates=CANDIDATES,
+                       rounds=2, use_cache=True, stream=None):
+    """Threads per CTA of the fastest sweep for this shape (timed on the current device)."""
+    ea = couplings[0] != "ferro"
+    key = _key(dim, L, R, ea, theta)
+    if use_cache:
+        _load()
+        if key in _CACHE:
+            return int(_CACHE[key])
+    n = rounds * len(candidates) + 1
+    betas = np.linspace(0.0, 0.5, n + 1)
+    thetas = np.full(n, theta, np.uint32)
+    run = pa.Population(dim, L, R, betas, thetas, "systematic", 12345, couplings=couplings,
+                        stream=stream)
+    run.step(1)  # first launch of each kernel outside the timings
+    best = {}
+    pa.pa_enable_timing(run.ctx, True)
+    for _ in range(rounds):
+        for t in candidates:
+            pa.pa_set_sweep_threads(run.ctx, t)
+            run.step(1)
+            ms, cnt, upd = pa.pa_sweep_timing(run.ctx)
+            rate = upd / max(ms, 1e-9)
+            best[t] = max(best.get(t, 0.0), rate)
+    run.close()
+    choice = max(best, key=best.get)
+    _CACHE[key] = int(choice)
+    if use_cache:
+        _save()
+    return int(choice)

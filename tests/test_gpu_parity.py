@@ -207,3 +207,24 @@ def test_checkpoint_restore_continues_bit_for_bit():
         assert b.free_energy() == ref.free_energy()
         ref.close()
         b.close()
+
+
+@pytest.mark.parametrize("d,L,kind", [(2, 64, "ferro"), (3, 6, "ea")])
+def test_sweep_launch_configuration_does_not_change_results(d, L, kind):
+    cpl, J = _couplings(d, L, kind)
+    betas = np.linspace(0, 1.0, 5)
+    th = np.full(4, 3, np.uint32)
+    ref = None
+    for t in (64, 128, 256, 512):
+        g = pa.Population(d, L, 200, betas, th, "nearest", 6, couplings=cpl, sweep_threads=t)
+        assert pa.pa_get_sweep_threads(g.ctx) == t
+        g.step(4)
+        cur = (g.spins_words(), g.families(), g.observables())
+        g.close()
+        if ref is None:
+            ref = cur
+        else:
+            assert np.array_equal(cur[0], ref[0]) and np.array_equal(cur[1], ref[1])
+            assert cur[2] == ref[2]
+    with pytest.raises(pa.PAError):
+        g = pa.Population(d, L, 10, betas, th, "nearest", 6, couplings=cpl, sweep_threads=96)
