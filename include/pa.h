@@ -92,7 +92,7 @@ typedef struct {
 typedef struct {
     int32_t n_steps;        /* number of temperature steps n >= 1                 */
     const double *beta;     /* host, n_steps + 1 values                            */
-    const uint32_t *theta;  /* host, n_steps values, each < 2^26                   */
+    const uint32_t *theta;  /* host, n_steps values, each < 2^24                   */
 } pa_schedule;
 
 /* Population averages after the sweeps of the current step (Sec. 2 step 4).

@@ -72,6 +72,9 @@ def lib():
             L.or_sweeps.argtypes = [C.c_int, C.c_int, i8p, i8p, i32p, C.c_uint64, C.c_uint32,
                                     C.c_uint32, C.c_uint32, u32p]
             L.or_sweeps.restype = C.c_uint64
+            L.or_u_less.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int,
+                                    C.c_int, C.c_uint32]
+            L.or_u_less.restype = C.c_int
             L.or_resample.argtypes = [i32p, C.c_uint32, C.c_uint32, C.c_double, C.c_int,
                                       C.c_uint64, C.c_uint32, u32p, u64p, dp, u64p]
             L.or_resample.restype = C.c_int
@@ -133,6 +136,11 @@ def init_replica(d, L, seed, j) -> np.ndarray:
     s = np.zeros(L ** d, np.int8)
     lib().or_init_replica(d, L, seed, j, _p(s, C.c_int8))
     return s
+
+
+def u_less(seed, slot, step, sweep, colour, site, thr) -> bool:
+    """The Metropolis test u < thr of one (replica slot, site, sweep, colour, step)."""
+    return bool(lib().or_u_less(seed, slot, step, sweep, colour, site, thr))
 
 
 def thresholds(beta: float) -> np.ndarray:

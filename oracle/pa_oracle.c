@@ -23,7 +23,8 @@
  *   - RNG: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = 64-bit
  *     seed, counter = (c0, c1, c2, c3) with the domain in the top bits of c1.
  *   - Metropolis accepts a move with dE > 0 iff u < thr[dE/4], u a uint32
- *     draw and thr[k] = floor(2^32 exp(-4 k beta)) (clamped to 2^32-1).
+ *     uniform and thr[k] = floor(2^32 exp(-4 k beta)) (clamped to 2^32-1);
+ *     the bits of u are bit planes shared by 32 consecutive replica slots.
  *   - The Boltzmann factors are evaluated per energy level,
  *     w_k = q^k with q = exp(-4 dbeta) by binary powering, summed in a fixed
  *     pairwise tree, and turned into 2^-40 fixed-point expected copy numbers
@@ -222,11 +223,33 @@ void or_thresholds(double beta, uint32_t thr[4])
     }
 }
 
+/* The uint32 uniform u of the Metropolis test of the replica in slot `slot`
+ * at site s (round t, colour c, temperature step `step`) is made of 32 bit
+ * planes: its bit 31 - p is bit (slot & 31) of plane word p, and plane word
+ * p is lane p & 3 of the SWEEP draw with counter
+ *   c0 = slot >> 5, c1 = (t << 4) | (c << 3) | (p >> 2), c2 = step, c3 = s.
+ * u < thr is decided by comparing u and thr four bits (one draw) at a time
+ * from the most significant end, which is the ordinary comparison of two
+ * numbers digit by digit in base 16; equal numbers are not "less". */
+int or_u_less(uint64_t seed, uint32_t slot, uint32_t step, uint32_t t, int c, int s,
+              uint32_t thr)
+{
+    uint32_t g, x[4], r = slot & 31u;
+    for (g = 0; g < 8; ++g) {
+        uint32_t du, dt;
+        draw4(seed, slot >> 5, DOM_SWEEP | (t << 4) | ((uint32_t)c << 3) | g, step, (uint32_t)s, x);
+        du = (((x[0] >> r) & 1u) << 3) | (((x[1] >> r) & 1u) << 2) |
+             (((x[2] >> r) & 1u) << 1) | ((x[3] >> r) & 1u);
+        dt = (thr >> (28 - 4 * g)) & 15u;
+        if (du != dt) return du < dt;
+    }
+    return 0;
+}
+
 /* Step 3: theta rounds of single-replica updates of the replica in slot
  * `slot` at temperature step `step`.  One round = all colour-0 sites in
- * ascending order, then all colour-1 sites.  The k-th site of a colour
- * (k = s >> 1, since L is even) uses lane k & 3 of the SWEEP draw with
- * c0 = k >> 2, c1 = (round << 1) | colour, c2 = step, c3 = slot.
+ * ascending order, then all colour-1 sites.  A site flips if dE <= 0, else
+ * iff u < thr[dE/4] with u the uniform above.
  * Returns the number of accepted flips; updates *E by the energy changes. */
 uint64_t or_sweeps(int d, int L, const int8_t *J, int8_t *sig, int32_t *E,
                    uint64_t seed, uint32_t step, uint32_t slot, uint32_t theta,
@@ -236,23 +259,18 @@ uint64_t or_sweeps(int d, int L, const int8_t *J, int8_t *sig, int32_t *E,
     uint64_t acc = 0;
     uint32_t t;
     int c, s, a;
-    uint32_t x[4];
     for (t = 0; t < theta; ++t) {
         for (c = 0; c < 2; ++c) {
             for (s = 0; s < N; ++s) {
-                int h = 0, dE, kk, flip;
-                uint32_t k;
+                int h = 0, dE, flip;
                 if (site_colour(d, L, s) != c) continue;
                 for (a = 0; a < d; ++a) {
                     h += J[a * N + s] * sig[nb_site(d, L, s, a, +1)];
                     h += J[a * N + nb_site(d, L, s, a, -1)] * sig[nb_site(d, L, s, a, -1)];
                 }
                 dE = 2 * sig[s] * h;
-                k = (uint32_t)(s >> 1);
-                draw4(seed, k >> 2, DOM_SWEEP | (t << 1) | (uint32_t)c, step, slot, x);
-                kk = dE / 4;
                 if (dE <= 0) flip = 1;
-                else flip = x[k & 3] < thr[kk];
+                else flip = or_u_less(seed, slot, step, t, c, s, thr[dE / 4]);
                 if (flip) {
                     sig[s] = (int8_t)-sig[s];
                     *E += dE;

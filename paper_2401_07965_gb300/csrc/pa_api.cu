@@ -216,7 +216,7 @@ pa_status pa_init(pa_ctx** out, const pa_lattice* lat, const pa_couplings* cpl, 
         if (!(sched->beta[i] > sched->beta[i - 1]) || !std::isfinite(sched->beta[i]))
             return PA_ERR_ARG;
     for (int i = 0; i < n; ++i)
-        if (sched->theta[i] >= (1u << 26)) return PA_ERR_ARG;
+        if (sched->theta[i] >= (1u << 24)) return PA_ERR_ARG;
     if (cpl->kind < 0 || cpl->kind > 2) return PA_ERR_ARG;
     if (cpl->kind == PA_COUPLING_EXPLICIT && !cpl->J) return PA_ERR_ARG;
 

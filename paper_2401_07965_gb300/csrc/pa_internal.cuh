@@ -3,7 +3,8 @@
 // Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), keyed
 // by the 64-bit run seed; the counter (c0, c1, c2, c3) carries the draw's
 // purpose in the top nibble of c1:
-//   sweep      c0 = site quad, c1 = (sweep << 1) | colour, c2 = step, c3 = slot
+//   sweep      c0 = slot >> 5, c1 = (sweep << 4) | (colour << 3) | plane block,
+//              c2 = step, c3 = site
 //   init       c0 = word >> 2, c1 = 1 << 28,             c2 = 0,    c3 = replica
 //   resample   c0 = index,     c1 = (2 << 28) | rule,    c2 = step, c3 = chunk
 //   disorder   c0 = bond >> 7, c1 = 3 << 28,             c2 = 0,    c3 = realization

@@ -13,10 +13,10 @@
 // the uniform draw and its threshold compare are per (replica, site).
 //
 // Metropolis at beta_i: for site s with n unsatisfied bonds out of 2d,
-// dE = 4 (d - n).  dE <= 0 flips; dE = 4k > 0 flips iff u < thr[k], u the
-// uint32 draw of Philox counter (quad, (sweep<<1)|colour, step, slot) lane
-// k&3 where k = s >> 1 is the index of s among the sites of its colour.
-// Colour 0 (x+y+z even) is updated before colour 1 in every sweep.
+// dE = 4 (d - n).  dE <= 0 flips; dE = 4k > 0 flips iff u < thr[k] with u a
+// uint32 uniform whose bits are bit planes shared by the CTA's 32 replicas
+// (see below).  Colour 0 (x+y+z even) is updated before colour 1 in every
+// sweep; thread k of a half-sweep updates the k-th site of the colour.
 //
 // After the sweeps the CTA recomputes E = 2U - dN (U = unsatisfied bonds)
 // and M, writes the 32 rows back, adds each replica to the energy-level
@@ -69,154 +69,152 @@ __global__ void k_init_spins(KParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// One quad of same-colour sites for the 32 replicas of the CTA.
+// Bit-plane uniforms.  The uniform u of replica r (slot base + r) at site s has
+// bit 31 - p equal to bit r of plane word p, the lane p & 3 of the Philox draw
+// with counter (base >> 5, (sweep << 4) | (colour << 3) | (p >> 2), step, s).
+// u < thr is decided from the most significant plane down; a replica leaves
+// the comparison at the first plane where u and thr differ, and the planes of
+// a site stop once all 32 replicas are decided.
+//
+// Of the 10 Philox rounds, those parts that depend only on the CTA's replica
+// group, the step, the sweep, the colour and the plane block g are the same
+// for every thread of the CTA: they are computed once per half-sweep into a
+// shared-memory table, together with the threshold bits of each plane as
+// all-ones / all-zeros masks.  Per site, rounds 2 and 3 need one wide multiply
+// each; per block of four planes, rounds 4-10 need 14.
 // ---------------------------------------------------------------------------
-template <int D, bool EA>
-__device__ __forceinline__ uint32_t update_quad(uint32_t* ms, const uint8_t* jb, const KParams& p,
-                                                int q, int colour, uint32_t c1v, uint32_t step,
-                                                uint32_t base, uint32_t vmask,
-                                                const uint32_t (&thr)[4]) {
-    const int L = p.L, N = p.N;
-    const int LL = L * L;
-    int sites[4];
-    uint32_t G[4][D];  // G[m][k-1]: replica needs u < thr[k] to flip (thermometer)
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const int k = 4 * q + m;
-        const int s0 = 2 * k;
-        if (s0 >= N) {
-            sites[m] = -1;
-#pragma unroll
-            for (int a = 0; a < D; ++a) G[m][a] = 0xFFFFFFFFu;
-            continue;
-        }
-        int q1 = div_L(s0, p);
-        int x = s0 - q1 * L, y, z = 0;
-        if (D == 3) {
-            z = div_L(q1, p);
-            y = q1 - z * L;
-        } else {
-            y = q1;
-        }
-        const int off = ((y + z) & 1) != colour;
-        const int s = s0 + off;
-        x += off;
-        sites[m] = s;
-        const int xp = (x == L - 1) ? s - (L - 1) : s + 1;
-        const int xm = (x == 0) ? s + (L - 1) : s - 1;
-        const int yp = (y == L - 1) ? s - (L - 1) * L : s + L;
-        const int ym = (y == 0) ? s + (L - 1) * L : s - L;
-        const uint32_t w = ms[s];
-        uint32_t P0 = w ^ ms[xp], P1 = w ^ ms[xm], P2 = w ^ ms[yp], P3 = w ^ ms[ym];
-        uint32_t P4 = 0, P5 = 0;
-        int zp = 0, zm = 0;
-        if (D == 3) {
-            zp = (z == L - 1) ? s - (L - 1) * LL : s + LL;
-            zm = (z == 0) ? s + (L - 1) * LL : s - LL;
-            P4 = w ^ ms[zp];
-            P5 = w ^ ms[zm];
-        }
-        if (EA) {
-            const uint32_t js = jb[s];
-            P0 ^= 0u - (js & 1u);
-            P1 ^= 0u - (uint32_t)(jb[xm] & 1u);
-            P2 ^= 0u - ((js >> 1) & 1u);
-            P3 ^= 0u - (uint32_t)((jb[ym] >> 1) & 1u);
-            if (D == 3) {
-                P4 ^= 0u - ((js >> 2) & 1u);
-                P5 ^= 0u - (uint32_t)((jb[zm] >> 2) & 1u);
-            }
-        }
-        if (D == 2) {
-            // n <= 1 and n == 0 over the 4 unsatisfied-bond planes
-            const uint32_t two = (P0 & P1) | (P2 & P3) | ((P0 | P1) & (P2 | P3));
-            G[m][0] = ~two;                     // dE > 0 needs n <= 1
-            G[m][D - 1] = ~(P0 | P1 | P2 | P3); // n == 0 : dE = 8
-        } else {
-            // bit-sliced 6-input count n = n0 + 2 n1 + 4 n2
-            const uint32_t sa = P0 ^ P1 ^ P2, ca = (P0 & P1) | (P2 & (P0 ^ P1));
-            const uint32_t sb = P3 ^ P4 ^ P5, cb = (P3 & P4) | (P5 & (P3 ^ P4));
-            const uint32_t n0 = sa ^ sb, kc = sa & sb;
-            const uint32_t n1 = ca ^ cb ^ kc, n2 = (ca & cb) | (kc & (ca ^ cb));
-            G[m][0] = ~n2 & ~(n1 & n0);  // n <= 2
-            G[m][1] = ~n2 & ~n1;         // n <= 1
-            G[m][D - 1] = ~(n0 | n1 | n2);  // n == 0
-        }
-    }
+struct PlaneTab {
+    uint32_t c0k, c1, c2k, pad;  // round-3 outputs that do not depend on the site
+    uint32_t B[4][4];            // B[m][k-1]: bit 31 - (4g + m) of thr[k] as a mask
+};
 
-    // Philox4x32-10 with counter (q, c1v, step, base + r): the first rounds
-    // do not depend on r and are evaluated once; the round keys come from the
-    // kernel parameters.
-    const uint32_t c0 = (uint32_t)q;
-    uint32_t h0a, l0a, h1a, l1a;
-    mulhilo(PHILOX_M0, c0, h0a, l0a);
+__device__ __forceinline__ void build_plane_tab(PlaneTab* tab, int g, const KParams& p,
+                                                uint32_t grp, uint32_t step, uint32_t t,
+                                                int colour, const uint32_t (&thr)[4]) {
+    uint32_t h0a, l0a, h1a, l1a, h0b, l0b, h1c, l1c;
+    mulhilo(PHILOX_M0, grp, h0a, l0a);
     mulhilo(PHILOX_M1, step, h1a, l1a);
-    const uint32_t A0 = h1a ^ c1v ^ p.rk0[0];   // round 1 outputs
-    const uint32_t A1 = l1a;
-    const uint32_t A2x = h0a ^ p.rk1[0] ^ base; // A2 = A2x ^ r
+    const uint32_t c1v = DOM_SWEEP | (t << 4) | ((uint32_t)colour << 3) | (uint32_t)g;
+    const uint32_t A0 = h1a ^ c1v ^ p.rk0[0];
     const uint32_t A3 = l0a;
-    uint32_t h0b, l0b;
-    mulhilo(PHILOX_M0, A0, h0b, l0b);           // round 2, lane 0
-    const uint32_t B1k = A1 ^ p.rk0[1];
-    const uint32_t B2 = h0b ^ A3 ^ p.rk1[1];    // round 2 outputs that do not depend on r
+    mulhilo(PHILOX_M0, A0, h0b, l0b);
+    const uint32_t B2 = h0b ^ A3 ^ p.rk1[1];
     const uint32_t B3 = l0b;
-    uint32_t h1c, l1c;
-    mulhilo(PHILOX_M1, B2, h1c, l1c);           // round 3, lane 2
-    const uint32_t C0k = h1c ^ p.rk0[2];
-    const uint32_t C2k = B3 ^ p.rk1[2];
-    const uint32_t C1 = l1c;
-
-    uint32_t T[4][D];
+    mulhilo(PHILOX_M1, B2, h1c, l1c);
+    PlaneTab e;
+    e.c0k = h1c ^ p.rk0[2];
+    e.c1 = l1c;
+    e.c2k = B3 ^ p.rk1[2];
+    e.pad = 0u;
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
-        for (int a = 0; a < D; ++a) T[m][a] = 0u;
+        for (int k = 0; k < 4; ++k)
+            e.B[m][k] = 0u - ((thr[(k + 1) & 3] >> (31 - (4 * g + m))) & 1u);
+    tab[g] = e;
+}
 
-#pragma unroll
-    for (int r = 0; r < 32; ++r) {
-        // round 2 (lane 2 depends on r)
-        const uint32_t A2 = A2x ^ (uint32_t)r;
-        uint32_t h1b, l1b;
+template <int D, bool EA>
+__device__ __forceinline__ uint32_t update_site(uint32_t* ms, const uint8_t* jb, const KParams& p,
+                                                int k, int colour, const PlaneTab* tab,
+                                                uint32_t A2x, uint32_t B1k, uint32_t vmask) {
+    const int L = p.L;
+    const int LL = L * L;
+    const int s0 = 2 * k;
+    int q1 = div_L(s0, p);
+    int x = s0 - q1 * L, y, z = 0;
+    if (D == 3) {
+        z = div_L(q1, p);
+        y = q1 - z * L;
+    } else {
+        y = q1;
+    }
+    const int off = ((y + z) & 1) != colour;
+    const int s = s0 + off;
+    x += off;
+    const int xp = (x == L - 1) ? s - (L - 1) : s + 1;
+    const int xm = (x == 0) ? s + (L - 1) : s - 1;
+    const int yp = (y == L - 1) ? s - (L - 1) * L : s + L;
+    const int ym = (y == 0) ? s + (L - 1) * L : s - L;
+    const uint32_t w = ms[s];
+    uint32_t P0 = w ^ ms[xp], P1 = w ^ ms[xm], P2 = w ^ ms[yp], P3 = w ^ ms[ym];
+    uint32_t P4 = 0, P5 = 0;
+    int zm = 0;
+    if (D == 3) {
+        const int zp = (z == L - 1) ? s - (L - 1) * LL : s + LL;
+        zm = (z == 0) ? s + (L - 1) * LL : s - LL;
+        P4 = w ^ ms[zp];
+        P5 = w ^ ms[zm];
+    }
+    if (EA) {
+        const uint32_t js = jb[s];
+        P0 ^= 0u - (js & 1u);
+        P1 ^= 0u - (uint32_t)(jb[xm] & 1u);
+        P2 ^= 0u - ((js >> 1) & 1u);
+        P3 ^= 0u - (uint32_t)((jb[ym] >> 1) & 1u);
+        if (D == 3) {
+            P4 ^= 0u - ((js >> 2) & 1u);
+            P5 ^= 0u - (uint32_t)((jb[zm] >> 2) & 1u);
+        }
+    }
+    // classes of dE = 4 (d - n), n unsatisfied bonds: cls[k-1] = replicas with dE = 4k
+    uint32_t need, cls[D];
+    if (D == 2) {
+        const uint32_t any = P0 | P1 | P2 | P3;
+        const uint32_t two = (P0 & P1) | (P2 & P3) | ((P0 | P1) & (P2 | P3));
+        need = ~two;               // n <= 1: dE > 0
+        cls[1] = ~any;             // n == 0: dE = 8
+        cls[0] = need & any;       // n == 1: dE = 4
+    } else {
+        const uint32_t sa = P0 ^ P1 ^ P2, ca = (P0 & P1) | (P2 & (P0 ^ P1));
+        const uint32_t sb = P3 ^ P4 ^ P5, cb = (P3 & P4) | (P5 & (P3 ^ P4));
+        const uint32_t n0 = sa ^ sb, kc = sa & sb;
+        const uint32_t n1 = ca ^ cb ^ kc, n2 = (ca & cb) | (kc & (ca ^ cb));
+        need = ~n2 & ~(n1 & n0);     // n <= 2
+        cls[2] = ~(n0 | n1 | n2);    // n == 0: dE = 12
+        cls[1] = ~n2 & ~n1 & n0;     // n == 1: dE = 8
+        cls[0] = ~n2 & n1 & ~n0;     // n == 2: dE = 4
+    }
+    need &= vmask;
+    uint32_t lt = 0u;
+    if (need) {
+        // rounds 2 and 3: the site-dependent halves
+        const uint32_t A2 = A2x ^ (uint32_t)s;
+        uint32_t h1b, l1b, h0c, l0c;
         mulhilo(PHILOX_M1, A2, h1b, l1b);
         const uint32_t B0 = h1b ^ B1k;
         const uint32_t B1 = l1b;
-        // round 3 (lane 0 depends on r)
-        uint32_t h0c, l0c;
         mulhilo(PHILOX_M0, B0, h0c, l0c);
-        uint32_t x0 = C0k ^ B1;
-        uint32_t x1 = C1;
-        uint32_t x2 = h0c ^ C2k;
-        uint32_t x3 = l0c;
+        uint32_t und = need;
+#pragma unroll 1
+        for (int g = 0; g < 8; ++g) {
+            const PlaneTab& e = tab[g];
+            uint32_t x0 = e.c0k ^ B1, x1 = e.c1, x2 = h0c ^ e.c2k, x3 = l0c;
 #pragma unroll
-        for (int rr = 3; rr < 10; ++rr) {
-            uint32_t hi0, lo0, hi1, lo1;
-            mulhilo(PHILOX_M0, x0, hi0, lo0);
-            mulhilo(PHILOX_M1, x2, hi1, lo1);
-            x0 = hi1 ^ x1 ^ p.rk0[rr];
-            x1 = lo1;
-            x2 = hi0 ^ x3 ^ p.rk1[rr];
-            x3 = lo0;
+            for (int rr = 3; rr < 10; ++rr) {
+                uint32_t hi0, lo0, hi1, lo1;
+                mulhilo(PHILOX_M0, x0, hi0, lo0);
+                mulhilo(PHILOX_M1, x2, hi1, lo1);
+                x0 = hi1 ^ x1 ^ p.rk0[rr];
+                x1 = lo1;
+                x2 = hi0 ^ x3 ^ p.rk1[rr];
+                x3 = lo0;
+            }
+            const uint32_t W[4] = {x0, x1, x2, x3};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                uint32_t tm = cls[0] & e.B[m][0];
+#pragma unroll
+                for (int a = 1; a < D; ++a) tm |= cls[a] & e.B[m][a];
+                lt |= und & tm & ~W[m];     // u bit 0, thr bit 1: u < thr
+                und &= ~(W[m] ^ tm);        // equal bits: still undecided
+            }
+            if (!und) break;
         }
-        const uint32_t u[4] = {x0, x1, x2, x3};
-        const uint32_t bit = 1u << r;
-#pragma unroll
-        for (int m = 0; m < 4; ++m)
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                if (u[m] < thr[a + 1]) T[m][a] |= bit;
     }
-
-    uint32_t acc = 0;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        if (sites[m] < 0) continue;
-        uint32_t f = vmask;
-#pragma unroll
-        for (int a = 0; a < D; ++a) f &= ~G[m][a] | T[m][a];
-        ms[sites[m]] ^= f;
-        acc += __popc(f);
-    }
-    return acc;
+    const uint32_t f = (~need | lt) & vmask;
+    ms[s] ^= f;
+    return (uint32_t)__popc(f);
 }
 
 // ---------------------------------------------------------------------------
@@ -232,6 +230,7 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
     __shared__ int32_t sU[32];
     __shared__ int32_t sNup[32];
     __shared__ unsigned long long sAcc;
+    __shared__ PlaneTab tabs[2][8];
 
     const DevState* st = p.st;
     if (st->status != S_OK) return;
@@ -282,15 +281,27 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
         uint32_t thr[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) thr[k] = p.thr[4 * (i - 1) + k];
-        const int nq = (N / 2 + 3) / 4;
-        for (uint32_t t = 0; t < theta; ++t) {
-            for (int colour = 0; colour < 2; ++colour) {
-                const uint32_t c1v = DOM_SWEEP | (t << 1) | (uint32_t)colour;
-                for (int q = threadIdx.x; q < nq; q += blockDim.x)
-                    acc += update_quad<D, EA>(ms, jb, p, q, colour, c1v, (uint32_t)i, base, vmask,
-                                              thr);
-                __syncthreads();
-            }
+        const uint32_t grp = base >> 5;
+        uint32_t h0a, l0a, h1a, l1a;
+        mulhilo(PHILOX_M0, grp, h0a, l0a);
+        mulhilo(PHILOX_M1, (uint32_t)i, h1a, l1a);
+        const uint32_t A2x = h0a ^ p.rk1[0];     // round-1 lane 2 without the site
+        const uint32_t B1k = l1a ^ p.rk0[1];     // round-2 lane 0 key part
+        const int nhalf = N / 2;
+        const uint32_t nh = 2u * theta;          // half-sweeps
+        if (nh > 0 && threadIdx.x < 8)
+            build_plane_tab(tabs[0], threadIdx.x, p, grp, (uint32_t)i, 0u, 0, thr);
+        __syncthreads();
+        for (uint32_t h = 0; h < nh; ++h) {
+            const int colour = (int)(h & 1u);
+            // the table of the next half-sweep goes to the other buffer
+            if (h + 1 < nh && threadIdx.x < 8)
+                build_plane_tab(tabs[(h + 1) & 1u], threadIdx.x, p, grp, (uint32_t)i,
+                                (h + 1) >> 1, (int)((h + 1) & 1u), thr);
+            const PlaneTab* tab = tabs[h & 1u];
+            for (int k = threadIdx.x; k < nhalf; k += blockDim.x)
+                acc += update_site<D, EA>(ms, jb, p, k, colour, tab, A2x, B1k, vmask);
+            __syncthreads();
         }
     }
 
@@ -380,9 +391,9 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
 }
 
 int sweep_threads(int N) {
-    const int nq = (N / 2 + 3) / 4;
+    const int sites = N / 2;  // per colour
     int t = 64;
-    while (t < nq && t < 256) t <<= 1;
+    while (t * 4 < sites && t < 256) t <<= 1;
     return t;
 }
 

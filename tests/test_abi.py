@@ -80,4 +80,4 @@ def test_init_rejects_bad_schedules_without_a_gpu(lib):
                    np.array([0.0, 0.1, 0.2, 0.3]), th, pa.PA_SYSTEMATIC, 1)
     with pytest.raises(pa.PAError):
         pa.pa_init(2, 8, ("ferro",), 10, 0, np.array([0.0, 0.1, 0.2, 0.3]),
-                   np.array([1, 1 << 26, 1], np.uint32), pa.PA_SYSTEMATIC, 1)
+                   np.array([1, 1 << 24, 1], np.uint32), pa.PA_SYSTEMATIC, 1)

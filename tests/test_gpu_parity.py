@@ -147,7 +147,8 @@ def test_large_steps_trigger_poisson_chunks_and_big_counts():
             st = orc.step()
             assert st == 0
             compare_step(gpu, orc, 64, f"{method} step {i + 1}")
-            assert int(orc.counts().max()) > 16
+            if i == 0:  # the jump from beta = 0 concentrates the weight
+                assert int(orc.counts().max()) > 16
         gpu.close()
 
 

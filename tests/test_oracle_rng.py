@@ -73,3 +73,38 @@ def test_own_exp_accuracy(oracle):
     assert worst < 4e-16
     assert oracle.exp(0.0) == 1.0
     assert oracle.exp(-math.log(2)) == pytest.approx(0.5, rel=2e-16)
+
+
+def _u_full(O, seed, slot, step, sweep, colour, site):
+    """u assembled bit by bit: bit 31-p is bit (slot & 31) of plane word p."""
+    u = 0
+    for p in range(32):
+        x = O.philox([slot >> 5, (sweep << 4) | (colour << 3) | (p >> 2), step, site],
+                     [seed & 0xFFFFFFFF, seed >> 32])
+        u |= ((int(x[p & 3]) >> (slot & 31)) & 1) << (31 - p)
+    return u
+
+
+def test_metropolis_uniform_digit_comparison_equals_full_comparison(oracle):
+    """The oracle decides u < thr four bits at a time from the top; that must equal the
+    comparison of the fully assembled 32-bit u, including thresholds close to u."""
+    rng = np.random.default_rng(4)
+    for _ in range(150):
+        seed = int(rng.integers(0, 2 ** 63))
+        slot, step = int(rng.integers(0, 5000)), int(rng.integers(1, 300))
+        sweep, colour, site = int(rng.integers(0, 10)), int(rng.integers(0, 2)), int(
+            rng.integers(0, 4096))
+        u = _u_full(oracle, seed, slot, step, sweep, colour, site)
+        for thr in (int(rng.integers(0, 2 ** 32)), u, u + 1, max(u - 1, 0), u ^ 1, u ^ 0x100,
+                    0, 0xFFFFFFFF):
+            thr &= 0xFFFFFFFF
+            assert oracle.u_less(seed, slot, step, sweep, colour, site, thr) == (u < thr)
+
+
+def test_metropolis_uniform_acceptance_rate(oracle):
+    """P(u < thr) = thr / 2^32 for the bit-plane uniforms."""
+    thr = int(0.3 * 2 ** 32)
+    hits = sum(oracle.u_less(7, slot, 3, 0, 0, site, thr)
+               for slot in range(0, 64) for site in range(0, 400, 2))
+    n = 64 * 200
+    assert abs(hits / n - 0.3) < 5 * math.sqrt(0.21 / n)
