@@ -114,10 +114,20 @@ __device__ __forceinline__ void build_plane_tab(PlaneTab* tab, int g, const KPar
     tab[g] = e;
 }
 
+// Site state of the plane comparison: the replicas still undecided, those
+// already known to have u < thr, the per-site Philox values and the masks of
+// the replicas in each energy class (cls[k-1]: dE = 4k).
+template <int D>
+struct SiteCmp {
+    int s;
+    uint32_t need, und, lt, B1, h0c, l0c;
+    uint32_t cls[D];
+};
+
 template <int D, bool EA>
-__device__ __forceinline__ uint32_t update_site(uint32_t* ms, const uint8_t* jb, const KParams& p,
-                                                int k, int colour, const PlaneTab* tab,
-                                                uint32_t A2x, uint32_t B1k, uint32_t vmask) {
+__device__ __forceinline__ void site_prepare(SiteCmp<D>& c, const uint32_t* ms, const uint8_t* jb,
+                                             const KParams& p, int k, int colour, uint32_t A2x,
+                                             uint32_t B1k, uint32_t vmask) {
     const int L = p.L;
     const int LL = L * L;
     const int s0 = 2 * k;
@@ -157,64 +167,105 @@ __device__ __forceinline__ uint32_t update_site(uint32_t* ms, const uint8_t* jb,
             P5 ^= 0u - (uint32_t)((jb[zm] >> 2) & 1u);
         }
     }
-    // classes of dE = 4 (d - n), n unsatisfied bonds: cls[k-1] = replicas with dE = 4k
-    uint32_t need, cls[D];
+    // classes of dE = 4 (d - n), n unsatisfied bonds
+    uint32_t need;
     if (D == 2) {
         const uint32_t any = P0 | P1 | P2 | P3;
         const uint32_t two = (P0 & P1) | (P2 & P3) | ((P0 | P1) & (P2 | P3));
-        need = ~two;               // n <= 1: dE > 0
-        cls[1] = ~any;             // n == 0: dE = 8
-        cls[0] = need & any;       // n == 1: dE = 4
+        need = ~two;                 // n <= 1: dE > 0
+        c.cls[D - 1] = ~any;         // n == 0: dE = 8
+        c.cls[0] = need & any;       // n == 1: dE = 4
     } else {
         const uint32_t sa = P0 ^ P1 ^ P2, ca = (P0 & P1) | (P2 & (P0 ^ P1));
         const uint32_t sb = P3 ^ P4 ^ P5, cb = (P3 & P4) | (P5 & (P3 ^ P4));
         const uint32_t n0 = sa ^ sb, kc = sa & sb;
         const uint32_t n1 = ca ^ cb ^ kc, n2 = (ca & cb) | (kc & (ca ^ cb));
-        need = ~n2 & ~(n1 & n0);     // n <= 2
-        cls[2] = ~(n0 | n1 | n2);    // n == 0: dE = 12
-        cls[1] = ~n2 & ~n1 & n0;     // n == 1: dE = 8
-        cls[0] = ~n2 & n1 & ~n0;     // n == 2: dE = 4
+        need = ~n2 & ~(n1 & n0);         // n <= 2
+        c.cls[D - 1] = ~(n0 | n1 | n2);  // n == 0: dE = 12
+        c.cls[1] = ~n2 & ~n1 & n0;       // n == 1: dE = 8
+        c.cls[0] = ~n2 & n1 & ~n0;       // n == 2: dE = 4
     }
-    need &= vmask;
-    uint32_t lt = 0u;
-    if (need) {
-        // rounds 2 and 3: the site-dependent halves
-        const uint32_t A2 = A2x ^ (uint32_t)s;
-        uint32_t h1b, l1b, h0c, l0c;
-        mulhilo(PHILOX_M1, A2, h1b, l1b);
-        const uint32_t B0 = h1b ^ B1k;
-        const uint32_t B1 = l1b;
-        mulhilo(PHILOX_M0, B0, h0c, l0c);
-        uint32_t und = need;
-#pragma unroll 1
-        for (int g = 0; g < 8; ++g) {
-            const PlaneTab& e = tab[g];
-            uint32_t x0 = e.c0k ^ B1, x1 = e.c1, x2 = h0c ^ e.c2k, x3 = l0c;
+    c.s = s;
+    c.need = need & vmask;
+    c.und = c.need;
+    c.lt = 0u;
+    // rounds 2 and 3: the site-dependent halves
+    const uint32_t A2 = A2x ^ (uint32_t)s;
+    uint32_t h1b, l1b;
+    mulhilo(PHILOX_M1, A2, h1b, l1b);
+    c.B1 = l1b;
+    mulhilo(PHILOX_M0, h1b ^ B1k, c.h0c, c.l0c);
+}
+
+// planes 4g..4g+3 of the comparison
+template <int D>
+__device__ __forceinline__ void plane_block(SiteCmp<D>& c, const PlaneTab& e, const KParams& p) {
+    uint32_t x0 = e.c0k ^ c.B1, x1 = e.c1, x2 = c.h0c ^ e.c2k, x3 = c.l0c;
 #pragma unroll
-            for (int rr = 3; rr < 10; ++rr) {
-                uint32_t hi0, lo0, hi1, lo1;
-                mulhilo(PHILOX_M0, x0, hi0, lo0);
-                mulhilo(PHILOX_M1, x2, hi1, lo1);
-                x0 = hi1 ^ x1 ^ p.rk0[rr];
-                x1 = lo1;
-                x2 = hi0 ^ x3 ^ p.rk1[rr];
-                x3 = lo0;
-            }
-            const uint32_t W[4] = {x0, x1, x2, x3};
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                uint32_t tm = cls[0] & e.B[m][0];
-#pragma unroll
-                for (int a = 1; a < D; ++a) tm |= cls[a] & e.B[m][a];
-                lt |= und & tm & ~W[m];     // u bit 0, thr bit 1: u < thr
-                und &= ~(W[m] ^ tm);        // equal bits: still undecided
-            }
-            if (!und) break;
-        }
+    for (int rr = 3; rr < 10; ++rr) {
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo(PHILOX_M0, x0, hi0, lo0);
+        mulhilo(PHILOX_M1, x2, hi1, lo1);
+        x0 = hi1 ^ x1 ^ p.rk0[rr];
+        x1 = lo1;
+        x2 = hi0 ^ x3 ^ p.rk1[rr];
+        x3 = lo0;
     }
-    const uint32_t f = (~need | lt) & vmask;
-    ms[s] ^= f;
+    const uint32_t W[4] = {x0, x1, x2, x3};
+    uint32_t und = c.und, lt = c.lt;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        uint32_t tm = c.cls[0] & e.B[m][0];
+#pragma unroll
+        for (int a = 1; a < D; ++a) tm |= c.cls[a] & e.B[m][a];
+        lt |= und & tm & ~W[m];  // u bit 0, thr bit 1: u < thr
+        und &= ~(W[m] ^ tm);     // equal bits: still undecided
+    }
+    c.und = und;
+    c.lt = lt;
+}
+
+template <int D>
+__device__ __forceinline__ uint32_t site_flip(const SiteCmp<D>& c, uint32_t* ms, uint32_t vmask) {
+    const uint32_t f = (~c.need | c.lt) & vmask;
+    ms[c.s] ^= f;
     return (uint32_t)__popc(f);
+}
+
+// queue of sites still undecided after the first two plane blocks (one per
+// CTA, struct of arrays in dynamic shared memory)
+template <int D>
+struct SiteQueue {
+    uint32_t* w;  // (7 + D) arrays of cap words
+    int cap;
+    __device__ void put(int e, const SiteCmp<D>& c) {
+        w[0 * cap + e] = (uint32_t)c.s;
+        w[1 * cap + e] = c.need;
+        w[2 * cap + e] = c.und;
+        w[3 * cap + e] = c.lt;
+        w[4 * cap + e] = c.B1;
+        w[5 * cap + e] = c.h0c;
+        w[6 * cap + e] = c.l0c;
+#pragma unroll
+        for (int a = 0; a < D; ++a) w[(7 + a) * cap + e] = c.cls[a];
+    }
+    __device__ void get(int e, SiteCmp<D>& c) const {
+        c.s = (int)w[0 * cap + e];
+        c.need = w[1 * cap + e];
+        c.und = w[2 * cap + e];
+        c.lt = w[3 * cap + e];
+        c.B1 = w[4 * cap + e];
+        c.h0c = w[5 * cap + e];
+        c.l0c = w[6 * cap + e];
+#pragma unroll
+        for (int a = 0; a < D; ++a) c.cls[a] = w[(7 + a) * cap + e];
+    }
+};
+
+// sites queued per half-sweep: a quarter of the sites of a colour, at least 32
+__host__ __device__ __forceinline__ int queue_capacity(int N) {
+    const int c = N / 8;
+    return c < 32 ? 32 : c;
 }
 
 // ---------------------------------------------------------------------------
@@ -227,10 +278,13 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t* ms = smem;
     uint8_t* jb = reinterpret_cast<uint8_t*>(smem + p.N);
+    const int qcap = queue_capacity(p.N);
+    uint32_t* qwords = smem + p.N + (p.ea ? (p.N + 15) / 16 * 4 : 0);
     __shared__ int32_t sU[32];
     __shared__ int32_t sNup[32];
     __shared__ unsigned long long sAcc;
     __shared__ PlaneTab tabs[2][8];
+    __shared__ int qn[2];
 
     const DevState* st = p.st;
     if (st->status != S_OK) return;
@@ -289,8 +343,15 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
         const uint32_t B1k = l1a ^ p.rk0[1];     // round-2 lane 0 key part
         const int nhalf = N / 2;
         const uint32_t nh = 2u * theta;          // half-sweeps
+        SiteQueue<D> queue;
+        queue.w = qwords;
+        queue.cap = qcap;
         if (nh > 0 && threadIdx.x < 8)
             build_plane_tab(tabs[0], threadIdx.x, p, grp, (uint32_t)i, 0u, 0, thr);
+        if (threadIdx.x == 0) {
+            qn[0] = 0;
+            qn[1] = 0;
+        }
         __syncthreads();
         for (uint32_t h = 0; h < nh; ++h) {
             const int colour = (int)(h & 1u);
@@ -298,9 +359,39 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
             if (h + 1 < nh && threadIdx.x < 8)
                 build_plane_tab(tabs[(h + 1) & 1u], threadIdx.x, p, grp, (uint32_t)i,
                                 (h + 1) >> 1, (int)((h + 1) & 1u), thr);
+            if (threadIdx.x == 0) qn[(h + 1) & 1u] = 0;
             const PlaneTab* tab = tabs[h & 1u];
-            for (int k = threadIdx.x; k < nhalf; k += blockDim.x)
-                acc += update_site<D, EA>(ms, jb, p, k, colour, tab, A2x, B1k, vmask);
+            // pass 1: every site runs plane blocks 0 and 1 (decides ~88% of sites)
+            for (int k = threadIdx.x; k < nhalf; k += blockDim.x) {
+                SiteCmp<D> c;
+                site_prepare<D, EA>(c, ms, jb, p, k, colour, A2x, B1k, vmask);
+                if (c.need) {
+                    plane_block<D>(c, tab[0], p);
+                    plane_block<D>(c, tab[1], p);
+                }
+                if (c.und) {
+                    const int e = atomicAdd(&qn[h & 1u], 1);
+                    if (e < qcap) {
+                        queue.put(e, c);
+                        continue;
+                    }
+                    for (int g = 2; g < 8 && c.und; ++g) plane_block<D>(c, tab[g], p);
+                }
+                acc += site_flip<D>(c, ms, vmask);
+            }
+            __syncthreads();
+            // pass 2: the undecided sites, one per thread, from plane block 2 on
+            const int nq = min(qn[h & 1u], qcap);
+            for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+                SiteCmp<D> c;
+                queue.get(e, c);
+#pragma unroll 1
+                for (int g = 2; g < 8; ++g) {
+                    plane_block<D>(c, tab[g], p);
+                    if (!c.und) break;
+                }
+                acc += site_flip<D>(c, ms, vmask);
+            }
             __syncthreads();
         }
     }
@@ -400,7 +491,9 @@ int sweep_threads(int N) {
 bool sweep_threads_supported(int t) { return t == 64 || t == 128 || t == 256 || t == 512; }
 
 static size_t group_smem(const KParams& p) {
-    return (size_t)p.N * 4 + (p.ea ? (size_t)((p.N + 15) / 16) * 16 : 0);
+    const size_t words_per_entry = 7 + (size_t)p.d;
+    return (size_t)p.N * 4 + (p.ea ? (size_t)((p.N + 15) / 16) * 16 : 0) +
+           words_per_entry * 4 * (size_t)queue_capacity(p.N);
 }
 
 template <int D, bool EA, int NT>
