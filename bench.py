@@ -43,11 +43,25 @@ RULES = ["multinomial", "systematic", "residual", "poisson", "nearest"]
 L, DIM, R, NSTEPS, THETA, SEED, BETA_F = 64, 2, 100_000, 200, 10, 7, 1.0
 WORKLOAD = ("2D Ising ferromagnet L=64 periodic, R=100000, beta 0->1 in 200 steps, theta=10, "
             "multinomial/systematic/residual/Poisson/nearest-integer runs, seed 7")
-# integer operations per spin update that the method itself requires: a quarter
-# of a Philox4x32-10 block (10 rounds x (2 wide multiplies + 2 three-input XORs)
-# = 40 operations per 4 draws) and the threshold compare
-OPS_PER_UPDATE = 11.0
-INT_LANES_PER_SM = 128  # 4 schedulers x 32 lanes issue one integer op per clock each
+# Roofline of the sweep kernel (integer ALU bound).  Per site word (one site of
+# the 32 replicas of a CTA) the bit-plane Metropolis test needs, with an ideal
+# per-site stop at the first deciding plane block, E_B Philox blocks, where
+# E_B = sum_g P(some replica undecided after 4g planes) = sum_g 1-(1-16^-g)^32.
+# Per block: 14 wide multiplies (rounds 4-10; rounds 1-3 are shared by the
+# counter layout) and 17 ALU operations (their 14 three-input XORs and 3 to
+# combine the shared halves), plus 5 ALU operations per plane (threshold mask
+# of the replica classes, the "less" and the "undecided" update) for d = 2.
+# Per site: 2 wide multiplies (rounds 2-3) and 12 ALU operations (four
+# neighbour XORs, the class masks, the flip).  ALU operations run on a pipe of
+# 64 lanes per clock per SM (ncu: sm__inst_executed_pipe_alu peak = 2 warp
+# instructions per cycle); wide multiplies on one of 32 per clock (probe).
+E_BLOCKS = sum(1.0 - (1.0 - 16.0 ** -g) ** 32 for g in range(8))
+ALU_OPS_PER_SITEWORD = 12 + E_BLOCKS * (17 + 4 * 5)
+MULWIDE_PER_SITEWORD = 2 + E_BLOCKS * 14
+ALU_OPS_PER_UPDATE = ALU_OPS_PER_SITEWORD / 32.0
+MULWIDE_PER_UPDATE = MULWIDE_PER_SITEWORD / 32.0
+ALU_LANES_PER_SM = 64
+MULWIDE_PER_SM = 32
 
 
 def _env_rank():
@@ -291,16 +305,21 @@ def run_ours(args):
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     clocks = clk.summary()
     f_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak_tops = nsm * INT_LANES_PER_SM * f_hz / 1e12
+    peak_alu = nsm * ALU_LANES_PER_SM * f_hz / 1e12           # T ALU ops / s
+    peak_mul = nsm * MULWIDE_PER_SM * f_hz / 1e12             # T wide multiplies / s
     sweep_rate = sweep_upd / (sweep_ms * 1e6)  # updates / ns inside the sweep kernel
-    achieved = OPS_PER_UPDATE * sweep_rate * 1e9 / 1e12
+    achieved = ALU_OPS_PER_UPDATE * sweep_rate * 1e9 / 1e12
     traffic_full = _sweep_traffic(_src_hash())
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-            "frac": achieved / peak_tops, "traffic": traffic_full,
-            "kernel": "k_group<2,false> (copy + theta sweeps + measurement)",
-            "peak_source": f"{nsm} SMs x {INT_LANES_PER_SM} int lanes x sm_max_mhz "
-                           f"({peak_src} clocks)",
-            "ops_per_update": OPS_PER_UPDATE, "sweep_updates_per_ns": sweep_rate,
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "Tops/s",
+            "frac": achieved / peak_alu, "traffic": traffic_full,
+            "kernel": "k_group<2,false,T> (gather + theta bit-plane Metropolis sweeps + measure)",
+            "peak_source": f"{nsm} SMs x {ALU_LANES_PER_SM} ALU-pipe lanes x sm_max_mhz "
+                           f"({peak_src} clocks); ALU-pipe lanes from ncu's pipe peak",
+            "alu_ops_per_update": ALU_OPS_PER_UPDATE,
+            "mulwide_per_update": MULWIDE_PER_UPDATE,
+            "mulwide_frac": MULWIDE_PER_UPDATE * sweep_rate * 1e9 / 1e12 / peak_mul,
+            "sweep_updates_per_ns": sweep_rate,
+            "roofline_updates_per_ns": peak_alu * 1e3 / ALU_OPS_PER_UPDATE,
             "sweep_share_of_step_time": sweep_ms / total_ms if world == 1 else None}
     cpu = None
     if not args.no_cpu_baseline and world == 1:

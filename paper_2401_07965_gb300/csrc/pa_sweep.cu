@@ -197,9 +197,10 @@ __device__ __forceinline__ void site_prepare(SiteCmp<D>& c, const uint32_t* ms, 
     mulhilo(PHILOX_M0, h1b ^ B1k, c.h0c, c.l0c);
 }
 
-// planes 4g..4g+3 of the comparison
+// rounds 4-10 of the draw of plane block g (its four plane words)
 template <int D>
-__device__ __forceinline__ void plane_block(SiteCmp<D>& c, const PlaneTab& e, const KParams& p) {
+__device__ __forceinline__ void block_draw(const SiteCmp<D>& c, const PlaneTab& e, const KParams& p,
+                                           uint32_t (&W)[4]) {
     uint32_t x0 = e.c0k ^ c.B1, x1 = e.c1, x2 = c.h0c ^ e.c2k, x3 = c.l0c;
 #pragma unroll
     for (int rr = 3; rr < 10; ++rr) {
@@ -211,7 +212,43 @@ __device__ __forceinline__ void plane_block(SiteCmp<D>& c, const PlaneTab& e, co
         x2 = hi0 ^ x3 ^ p.rk1[rr];
         x3 = lo0;
     }
-    const uint32_t W[4] = {x0, x1, x2, x3};
+    W[0] = x0;
+    W[1] = x1;
+    W[2] = x2;
+    W[3] = x3;
+}
+
+// two independent blocks, rounds interleaved for instruction-level parallelism
+template <int D>
+__device__ __forceinline__ void block_draw2(const SiteCmp<D>& c, const PlaneTab& e,
+                                            const PlaneTab& f, const KParams& p,
+                                            uint32_t (&W)[4], uint32_t (&V)[4]) {
+    uint32_t x0 = e.c0k ^ c.B1, x1 = e.c1, x2 = c.h0c ^ e.c2k, x3 = c.l0c;
+    uint32_t y0 = f.c0k ^ c.B1, y1 = f.c1, y2 = c.h0c ^ f.c2k, y3 = c.l0c;
+#pragma unroll
+    for (int rr = 3; rr < 10; ++rr) {
+        uint32_t hi0, lo0, hi1, lo1, gi0, go0, gi1, go1;
+        mulhilo(PHILOX_M0, x0, hi0, lo0);
+        mulhilo(PHILOX_M1, x2, hi1, lo1);
+        mulhilo(PHILOX_M0, y0, gi0, go0);
+        mulhilo(PHILOX_M1, y2, gi1, go1);
+        x0 = hi1 ^ x1 ^ p.rk0[rr];
+        x1 = lo1;
+        x2 = hi0 ^ x3 ^ p.rk1[rr];
+        x3 = lo0;
+        y0 = gi1 ^ y1 ^ p.rk0[rr];
+        y1 = go1;
+        y2 = gi0 ^ y3 ^ p.rk1[rr];
+        y3 = go0;
+    }
+    W[0] = x0; W[1] = x1; W[2] = x2; W[3] = x3;
+    V[0] = y0; V[1] = y1; V[2] = y2; V[3] = y3;
+}
+
+// compare four planes: replicas leave at the first plane where u and thr differ
+template <int D>
+__device__ __forceinline__ void block_compare(SiteCmp<D>& c, const PlaneTab& e,
+                                              const uint32_t (&W)[4]) {
     uint32_t und = c.und, lt = c.lt;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -223,6 +260,13 @@ __device__ __forceinline__ void plane_block(SiteCmp<D>& c, const PlaneTab& e, co
     }
     c.und = und;
     c.lt = lt;
+}
+
+template <int D>
+__device__ __forceinline__ void plane_block(SiteCmp<D>& c, const PlaneTab& e, const KParams& p) {
+    uint32_t W[4];
+    block_draw<D>(c, e, p, W);
+    block_compare<D>(c, e, W);
 }
 
 template <int D>
@@ -366,8 +410,10 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
                 SiteCmp<D> c;
                 site_prepare<D, EA>(c, ms, jb, p, k, colour, A2x, B1k, vmask);
                 if (c.need) {
-                    plane_block<D>(c, tab[0], p);
-                    plane_block<D>(c, tab[1], p);
+                    uint32_t W[4], V[4];
+                    block_draw2<D>(c, tab[0], tab[1], p, W, V);
+                    block_compare<D>(c, tab[0], W);
+                    block_compare<D>(c, tab[1], V);
                 }
                 if (c.und) {
                     const int e = atomicAdd(&qn[h & 1u], 1);
