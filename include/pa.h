@@ -117,6 +117,37 @@ typedef struct {
     double accept_rate;    /* accepts / (theta_i N R_i)                             */
 } pa_obs;
 
+/* One run of a batch (pa_batch_init).  All runs of a batch share the
+ * dimension, the coupling kind (ferromagnet or not), the copy-count rule, the
+ * schedule and the Philox key; lattice size, couplings, R and R_cap are per
+ * run.  Runs with the same ensemble id must repeat one system (same lattice
+ * and couplings): pa_weighted combines them (Sec. 4). */
+typedef struct {
+    pa_lattice lattice;
+    pa_couplings couplings;
+    uint32_t R;
+    uint32_t R_cap;          /* 0 = default capacity                               */
+    int32_t ensemble;        /* >= 0                                              */
+} pa_run_spec;
+
+/* Weighted average over the runs of one ensemble at one temperature step,
+ * with omega^(m) = R_i^(m) exp(-beta_i F_i^(m)) / sum (Eq. weighted-averages). */
+typedef struct {
+    int32_t step;
+    int32_t n_runs;
+    double beta;
+    double lnZ;           /* ln( sum_m R^(m) Zhat_m / sum_m R^(m) ) - ln Z_0          */
+    double minus_beta_F;  /* N ln 2 + lnZ                                          */
+    double w_max;         /* largest omega                                         */
+    double eff_runs;      /* 1 / sum omega^2                                        */
+    double e, e2, absm, m2;   /* W[e], W[e^2], W[|m|], W[m^2]                        */
+    double c;             /* Wvar[c] = beta^2 N (W[e^2] - W[e]^2), Eq. (Wvar_C)     */
+    double chi;           /* Wvar[chi] = beta N (W[m^2] - W[|m|]^2), Eq. (Wvar_Chi) */
+    double c_naive;       /* sum_m omega c^(m) (the naive weighting)               */
+    double chi_naive;     /* sum_m omega chi^(m)                                   */
+    double e_plain, c_plain, chi_plain;  /* unweighted means over the runs          */
+} pa_weighted_obs;
+
 /* Arrays readable with pa_get_array. */
 typedef enum {
     PA_ARRAY_SPINS = 0,      /* uint32 [R_i][ceil(N/32)] packed spins              */
@@ -229,6 +260,37 @@ int32_t pa_get_sweep_threads(const pa_ctx *ctx);
 pa_status pa_weights_static(const int32_t *E, uint32_t R_prev, uint32_t R, int32_t dim, int32_t L,
                             int32_t parity, double dbeta, double *lnQ, uint64_t *f,
                             void *cuda_stream);
+
+/* ---- batches of runs ------------------------------------------------------
+ *
+ * A batch advances M independent runs with the same kernels (one launch per
+ * phase for all runs).  Run m's draws use the context's seed with run m's
+ * identity in the counter: its sweep and initial draws use replica slots
+ * offset by 32 x (the sweep CTAs of runs 0..m-1) and its resampling draws carry
+ * m; a batch of one run is identical to pa_init.  The single-run calls above
+ * act on run 0; pa_set_state needs M = 1. */
+size_t pa_batch_workspace_bytes(const pa_run_spec *runs, int32_t M, int32_t n_steps,
+                                pa_resampler resampler);
+pa_status pa_batch_init(pa_ctx **out, const pa_run_spec *runs, int32_t M,
+                        const pa_schedule *sched, pa_resampler resampler, uint64_t seed,
+                        void *cuda_stream, void *workspace, size_t workspace_bytes);
+int32_t pa_batch_size(const pa_ctx *ctx);
+pa_status pa_run_observables(pa_ctx *ctx, int32_t run, pa_obs *out);
+pa_status pa_run_trace(pa_ctx *ctx, int32_t run, pa_obs *rows, int32_t max_rows,
+                       int32_t *n_rows);
+pa_status pa_run_free_energy(pa_ctx *ctx, int32_t run, double *minus_beta_F, double *f_per_spin);
+pa_status pa_run_get_array(pa_ctx *ctx, int32_t run, pa_array which, void *host, size_t capacity,
+                           size_t *n_out);
+
+/* Synchronise, reduce on the device and copy rows 0..step of the weighted
+ * averages of the runs whose ensemble id is `ensemble` (Sec. 4).
+ * PA_ERR_ARG if no run has that id. */
+pa_status pa_weighted(pa_ctx *ctx, int32_t ensemble, pa_weighted_obs *rows, int32_t max_rows,
+                      int32_t *n_rows);
+
+/* Replay each temperature step as one captured CUDA graph (default on; needs a
+ * non-NULL stream; timing mode launches directly). */
+pa_status pa_set_graph(pa_ctx *ctx, int32_t on);
 
 /* Release the context (and the device memory it allocated).  NULL is a no-op. */
 pa_status pa_destroy(pa_ctx *ctx);

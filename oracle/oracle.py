@@ -76,11 +76,15 @@ def lib():
                                     C.c_int, C.c_uint32]
             L.or_u_less.restype = C.c_int
             L.or_resample.argtypes = [i32p, C.c_uint32, C.c_uint32, C.c_double, C.c_int,
-                                      C.c_uint64, C.c_uint32, u32p, u64p, dp, u64p]
+                                      C.c_uint64, C.c_uint32, C.c_uint32, u32p, u64p, dp, u64p]
             L.or_resample.restype = C.c_int
             L.or_run_create.argtypes = [C.c_int, C.c_int, i8p, C.c_uint32, C.c_uint32, C.c_int,
                                         dp, u32p, C.c_int, C.c_uint64]
             L.or_run_create.restype = C.c_void_p
+            L.or_run_create_ex.argtypes = [C.c_int, C.c_int, i8p, C.c_uint32, C.c_uint32,
+                                           C.c_int, dp, u32p, C.c_int, C.c_uint64, C.c_uint32,
+                                           C.c_uint32]
+            L.or_run_create_ex.restype = C.c_void_p
             L.or_run_destroy.argtypes = [C.c_void_p]
             L.or_run_step.argtypes = [C.c_void_p]
             L.or_run_step.restype = C.c_int
@@ -160,7 +164,7 @@ def sweeps(d, L, J, sig, seed, step, slot, theta, beta):
     return s, int(E[0]), int(acc)
 
 
-def resample(E, R, dbeta, method, seed, step):
+def resample(E, R, dbeta, method, seed, step, run_id=0):
     """Weights, ln Q and copy counts from energies E at one temperature step."""
     E = np.ascontiguousarray(E, np.int32)
     n = len(E)
@@ -169,7 +173,7 @@ def resample(E, R, dbeta, method, seed, step):
     lnQ = np.zeros(1, np.float64)
     Rnew = np.zeros(1, np.uint64)
     st = lib().or_resample(_p(E, C.c_int32), n, R, float(dbeta), int(method), seed, step,
-                           _p(counts, C.c_uint32), _p(f, C.c_uint64), _p(lnQ, C.c_double),
+                           run_id, _p(counts, C.c_uint32), _p(f, C.c_uint64), _p(lnQ, C.c_double),
                            _p(Rnew, C.c_uint64))
     return {"status": st, "counts": counts, "f": f, "lnQ": float(lnQ[0]), "R_new": int(Rnew[0])}
 
@@ -177,14 +181,15 @@ def resample(E, R, dbeta, method, seed, step):
 class Run:
     """A whole PA run of the oracle: Run(...).step() advances one temperature step."""
 
-    def __init__(self, d, L, J, R, betas, thetas, method, seed, R_cap=0):
+    def __init__(self, d, L, J, R, betas, thetas, method, seed, R_cap=0, slot_base=0, run_id=0):
         self.d, self.L, self.N = d, L, L ** d
         self.J = np.ascontiguousarray(J, np.int8)
         self.betas = np.ascontiguousarray(betas, np.float64)
         self.thetas = np.ascontiguousarray(thetas, np.uint32)
-        self._h = lib().or_run_create(d, L, _p(self.J, C.c_int8), R, R_cap,
-                                      len(self.betas) - 1, _p(self.betas, C.c_double),
-                                      _p(self.thetas, C.c_uint32), int(method), seed)
+        self._h = lib().or_run_create_ex(d, L, _p(self.J, C.c_int8), R, R_cap,
+                                         len(self.betas) - 1, _p(self.betas, C.c_double),
+                                         _p(self.thetas, C.c_uint32), int(method), seed,
+                                         slot_base, run_id)
         if not self._h:
             raise ValueError("oracle: invalid run arguments")
         self.R = R

@@ -323,15 +323,18 @@ static uint32_t find_box(const uint64_t *C, uint32_t n, uint64_t p)
 }
 
 /*
- * Resampling from beta_{i-1} to beta_i = beta_{i-1} + dbeta.
+ * Resampling from beta_{i-1} to beta_i = beta_{i-1} + dbeta.  run_id enters
+ * the resampling draws' counter (c1 = 2 << 28 | run_id << 8 | rule), so that
+ * runs advanced together draw independent numbers; a lone run has run_id 0.
  * Inputs: E[0..Rprev) (energies at beta_{i-1}), nominal size R, method.
  * Outputs: counts[0..Rprev), f_rep[0..Rprev) (2^-40 fixed-point tau-hat),
  * *lnQ, *Rnew.  Returns a status code.
  */
 int or_resample(const int32_t *E, uint32_t Rprev, uint32_t R, double dbeta,
-                int method, uint64_t seed, uint32_t step,
+                int method, uint64_t seed, uint32_t step, uint32_t run_id,
                 uint32_t *counts, uint64_t *f_rep, double *lnQ, uint64_t *Rnew)
 {
+    const uint32_t dom = DOM_RESAMPLE | (run_id << 8);
     int32_t Emin = E[0], Emax = E[0];
     uint32_t j, K, P, k, h;
     uint64_t *nlev, *flev, *C, T = 0, total = 0;
@@ -381,7 +384,7 @@ int or_resample(const int32_t *E, uint32_t Rprev, uint32_t R, double dbeta,
         /* floor(tau) copies plus one more with probability tau - floor(tau) */
         for (j = 0; j < Rprev; ++j) {
             uint64_t u40, frac;
-            draw4(seed, j, DOM_RESAMPLE | SUB_NEAREST, step, 0u, x);
+            draw4(seed, j, dom | SUB_NEAREST, step, 0u, x);
             u40 = (((uint64_t)x[1] << 32) | x[0]) >> 24;
             frac = f_rep[j] & ((1ull << FRAC_BITS) - 1);
             counts[j] = (uint32_t)(f_rep[j] >> FRAC_BITS) + (u40 < frac ? 1u : 0u);
@@ -390,7 +393,7 @@ int or_resample(const int32_t *E, uint32_t Rprev, uint32_t R, double dbeta,
         /* one uniform U in [0,1); labels at (k + U) T/R on the cumulative
          * weight axis; replica j takes the labels in [C_{j-1}, C_j). */
         uint64_t prev = 0, below_prev = 0;
-        draw4(seed, 0u, DOM_RESAMPLE | SUB_SYSTEMATIC, step, 0u, x);
+        draw4(seed, 0u, dom | SUB_SYSTEMATIC, step, 0u, x);
         for (j = 0; j < Rprev; ++j) {
             uint64_t below = sys_below(C[j], R, T, x[0]);
             counts[j] = (uint32_t)(below - below_prev);
@@ -403,7 +406,7 @@ int or_resample(const int32_t *E, uint32_t Rprev, uint32_t R, double dbeta,
         uint32_t kk;
         for (kk = 0; kk < R; ++kk) {
             uint64_t u64, p;
-            draw4(seed, kk >> 1, DOM_RESAMPLE | SUB_MULTINOMIAL, step, 0u, x);
+            draw4(seed, kk >> 1, dom | SUB_MULTINOMIAL, step, 0u, x);
             u64 = (kk & 1u) ? (((uint64_t)x[3] << 32) | x[2]) : (((uint64_t)x[1] << 32) | x[0]);
             p = (uint64_t)(((u128)u64 * T) >> 64);
             counts[find_box(C, Rprev, p)] += 1;
@@ -427,7 +430,7 @@ int or_resample(const int32_t *E, uint32_t Rprev, uint32_t R, double dbeta,
         boxT = (Tres > 0) ? Tres : T;
         for (kk = 0; kk < (uint32_t)Rres; ++kk) {
             uint64_t u64, p;
-            draw4(seed, kk >> 1, DOM_RESAMPLE | SUB_RESIDUAL, step, 0u, x);
+            draw4(seed, kk >> 1, dom | SUB_RESIDUAL, step, 0u, x);
             u64 = (kk & 1u) ? (((uint64_t)x[3] << 32) | x[2]) : (((uint64_t)x[1] << 32) | x[0]);
             p = (uint64_t)(((u128)u64 * boxT) >> 64);
             counts[find_box(box, Rprev, p)] += 1;
@@ -445,7 +448,7 @@ int or_resample(const int32_t *E, uint32_t Rprev, uint32_t R, double dbeta,
             for (m = 0; m < M; ++m) {
                 double u, p, Pc;
                 uint32_t kp = 0;
-                draw4(seed, j, DOM_RESAMPLE | SUB_POISSON, step, m, x);
+                draw4(seed, j, dom | SUB_POISSON, step, m, x);
                 u = ldexp((double)((((uint64_t)x[1] << 32) | x[0]) >> 11), -53);
                 p = or_exp(-lc);
                 Pc = p;
@@ -488,6 +491,8 @@ typedef struct {
     uint32_t *theta;
     int method;
     uint64_t seed;
+    uint32_t slot_base;   /* 32 x the replica groups of the runs before this one */
+    uint32_t run_id;
     int step;
     uint32_t Rcur, Rprev;
     int8_t *sig, *sig2;
@@ -544,13 +549,18 @@ static void measure(or_run *r, const uint32_t *counts, const uint64_t *f_rep, ui
     free(fc);
 }
 
-or_run *or_run_create(int d, int L, const int8_t *J, uint32_t R, uint32_t Rcap, int n_steps,
-                      const double *beta, const uint32_t *theta, int method, uint64_t seed)
+/* A run that is one of several advanced together: its replica slots are offset
+ * by slot_base (a multiple of 32) in the sweep and initial draws, and its
+ * resampling draws carry run_id.  slot_base = run_id = 0 is a lone run. */
+or_run *or_run_create_ex(int d, int L, const int8_t *J, uint32_t R, uint32_t Rcap, int n_steps,
+                         const double *beta, const uint32_t *theta, int method, uint64_t seed,
+                         uint32_t slot_base, uint32_t run_id)
 {
     or_run *r;
     uint32_t j;
     int N;
-    if (d < 2 || d > 3 || L < 2 || (L & 1) || R == 0 || n_steps < 0) return NULL;
+    if (d < 2 || d > 3 || L < 2 || (L & 1) || R == 0 || n_steps < 0 || (slot_base & 31u))
+        return NULL;
     r = (or_run *)calloc(1, sizeof(or_run));
     N = npow(L, d);
     r->d = d; r->L = L; r->N = N;
@@ -565,6 +575,8 @@ or_run *or_run_create(int d, int L, const int8_t *J, uint32_t R, uint32_t Rcap, 
     if (n_steps > 0) memcpy(r->theta, theta, sizeof(uint32_t) * n_steps);
     r->method = method;
     r->seed = seed;
+    r->slot_base = slot_base;
+    r->run_id = run_id;
     r->sig = (int8_t *)malloc((size_t)r->Rcap * N);
     r->sig2 = (int8_t *)malloc((size_t)r->Rcap * N);
     r->E = (int32_t *)malloc(sizeof(int32_t) * r->Rcap);
@@ -576,7 +588,7 @@ or_run *or_run_create(int d, int L, const int8_t *J, uint32_t R, uint32_t Rcap, 
     r->anc = (uint32_t *)calloc(r->Rcap, sizeof(uint32_t));
     /* step 1 */
     for (j = 0; j < R; ++j) {
-        or_init_replica(d, L, seed, j, r->sig + (size_t)j * N);
+        or_init_replica(d, L, seed, slot_base + j, r->sig + (size_t)j * N);
         r->E[j] = or_energy(d, L, r->J, r->sig + (size_t)j * N);
         r->fam[j] = j;
     }
@@ -586,6 +598,12 @@ or_run *or_run_create(int d, int L, const int8_t *J, uint32_t R, uint32_t Rcap, 
     r->sum_lnQ = 0.0;
     measure(r, NULL, NULL, 0, 0.0, 0);
     return r;
+}
+
+or_run *or_run_create(int d, int L, const int8_t *J, uint32_t R, uint32_t Rcap, int n_steps,
+                      const double *beta, const uint32_t *theta, int method, uint64_t seed)
+{
+    return or_run_create_ex(d, L, J, R, Rcap, n_steps, beta, theta, method, seed, 0u, 0u);
 }
 
 void or_run_destroy(or_run *r)
@@ -613,7 +631,7 @@ int or_run_step(or_run *r)
     i = r->step + 1;
     dbeta = r->beta[i] - r->beta[i - 1];
     /* step 2: resample */
-    st = or_resample(r->E, Rprev, r->R, dbeta, r->method, r->seed, (uint32_t)i,
+    st = or_resample(r->E, Rprev, r->R, dbeta, r->method, r->seed, (uint32_t)i, r->run_id,
                      r->counts, r->f_rep, &lnQ, &Rnew);
     if (st) { r->status = st; return st; }
     /* a population that outgrows its capacity, or dies out, stops the run */
@@ -639,7 +657,7 @@ int or_run_step(or_run *r)
     or_thresholds(r->beta[i], thr);
     for (j = 0; j < r->Rcur; ++j)
         acc += or_sweeps(r->d, r->L, r->J, r->sig + (size_t)j * N, &r->E[j], r->seed,
-                         (uint32_t)i, j, r->theta[i - 1], thr);
+                         (uint32_t)i, r->slot_base + j, r->theta[i - 1], thr);
     r->step = i;
     /* step 4: measure */
     measure(r, r->counts, r->f_rep, Rprev, lnQ, acc);

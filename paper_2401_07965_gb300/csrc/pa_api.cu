@@ -1,6 +1,7 @@
-// pa_api.cu -- the C ABI of include/pa.h: context, device workspace, host
-// precomputation of the per-step tables, and the launch sequence of a
-// temperature step (Sec. 2 steps 2-4).
+// pa_api.cu -- the C ABI of include/pa.h: contexts (batches of runs), device
+// workspace, host precomputation of the per-step tables, and the launch
+// sequence of a temperature step (Sec. 2 steps 2-4), replayed as a CUDA graph.
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -10,103 +11,163 @@
 #include "../../include/pa.h"
 #include "pa_internal.cuh"
 
+namespace pa {
+cudaError_t launch_weighted(const KParams& p, const int32_t* run_ids, int n_runs, int n_rows,
+                            pa_weighted_obs* out, cudaStream_t s);
+}
+
 using namespace pa;
+
+namespace {
+
+struct RunHost {
+    int L, N, W, Wp, nlev, P;
+    uint32_t R, Rcap;
+    int nblk, ngrp;
+    int ensemble;
+    std::vector<uint8_t> jb;
+    int parity;
+};
+
+enum Region {
+    R_SPIN0, R_SPIN1, R_E0, R_E1, R_F0, R_F1, R_M, R_ANC, R_CNT, R_C, R_G, R_HIST, R_FLEV, R_TREE,
+    R_PA, R_PB, R_OA, R_OB, R_PD, R_PCL, R_JB, R_ST, R_TRACE, R_COUNT
+};
+
+enum Shared { S_RUNS, S_B2R, S_G2R, S_BETA, S_DBETA, S_Q, S_THR, S_THETA, S_IDS, S_WOUT, S_COUNT };
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t shared_off[S_COUNT];
+    std::vector<std::array<size_t, R_COUNT>> run_off;
+    size_t total = 0;
+};
+
+}  // namespace
 
 struct pa_ctx {
     KParams kp;
-    int d = 0, L = 0, N = 0, W = 0, Wp = 0;
-    uint32_t R = 0, Rcap = 0;
-    int n_steps = 0, method = 0;
+    std::vector<RunHost> runs;
+    std::vector<RunDesc> desc;
+    int d = 0, n_steps = 0, method = 0, M = 0;
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
     void* ws = nullptr;
     size_t ws_bytes = 0;
     bool owns = false;
     int host_step = 0;
-    int threads = 32;
+    int threads = 64;
     int64_t launches = 0;
     pa_status sticky = PA_OK;
     bool timing = false;
+    bool use_graph = true;
+    cudaGraphExec_t graph = nullptr;
+    int graph_threads = 0;
+    int64_t graph_kernels = 0;
     std::vector<cudaEvent_t> ev_start, ev_stop;
     std::vector<int> timed_steps;
     std::vector<double> beta;
     std::vector<uint32_t> theta;
+    int32_t* d_ids = nullptr;               // run index list for pa_weighted (device)
+    pa_weighted_obs* d_wout = nullptr;      // its output rows (device)
 };
 
 namespace {
 
-struct Layout {
-    size_t off[40];
-    size_t total;
-};
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-struct Dims {
-    int d, L, N, W, Wp, nlev, P, nblk;
-    uint32_t R, Rcap;
-    int n_steps;
-};
-
-bool make_dims(const pa_lattice* lat, uint32_t R, uint32_t R_cap, int32_t n_steps, int method,
-               Dims* o) {
+bool check_lattice(const pa_lattice* lat, long long* N) {
     if (!lat || lat->dim < 2 || lat->dim > 3 || lat->L < 2 || (lat->L & 1)) return false;
-    if (R == 0 || n_steps < 1 || method < 0 || method > 4) return false;
-    long long N = 1;
-    for (int a = 0; a < lat->dim; ++a) N *= lat->L;
-    if (N > 32768) return false;  // the sweep keeps a lattice of 32 replicas in shared memory
-    o->d = lat->dim;
-    o->L = lat->L;
-    o->N = (int)N;
-    o->W = (int)((N + 31) / 32);
-    o->Wp = (o->W + 3) & ~3;
-    o->nlev = (int)(o->d * N / 2 + 1);
-    o->P = 1;
-    while (o->P < o->nlev) o->P <<= 1;
-    uint32_t cap = R_cap;
-    if (cap == 0) {
-        if (method == PA_POISSON || method == PA_NEAREST)
-            cap = R + (uint32_t)std::ceil(10.0 * std::sqrt((double)R)) + 64u;
-        else
-            cap = R;
-    }
-    if (cap < R || cap > (1u << 30)) return false;
-    o->R = R;
-    o->Rcap = cap;
-    o->nblk = (int)((cap + SCAN_CHUNK - 1) / SCAN_CHUNK);
-    o->n_steps = n_steps;
+    long long n = 1;
+    for (int a = 0; a < lat->dim; ++a) n *= lat->L;
+    if (n > 32768) return false;  // the sweep keeps a lattice of 32 replicas in shared memory
+    *N = n;
     return true;
 }
 
-enum Region {
-    R_SPIN0, R_SPIN1, R_E0, R_E1, R_F0, R_F1, R_M, R_ANC, R_CNT, R_C, R_G, R_HIST, R_FLEV, R_TREE,
-    R_PA, R_PB, R_OA, R_OB, R_PD, R_PC2, R_PCL, R_JB, R_BETA, R_DBETA, R_Q, R_THR, R_THETA, R_ST,
-    R_TRACE, R_COUNT
-};
+uint32_t default_cap(uint32_t R, int method) {
+    if (method == PA_POISSON || method == PA_NEAREST)
+        return R + (uint32_t)std::ceil(10.0 * std::sqrt((double)R)) + 64u;
+    return R;
+}
 
-Layout make_layout(const Dims& m) {
-    size_t sz[R_COUNT];
-    const size_t rows = (size_t)m.Rcap;
-    sz[R_SPIN0] = sz[R_SPIN1] = rows * m.Wp * 4;
-    sz[R_E0] = sz[R_E1] = sz[R_F0] = sz[R_F1] = sz[R_M] = sz[R_ANC] = sz[R_CNT] = rows * 4;
-    sz[R_C] = sz[R_G] = rows * 8;
-    sz[R_HIST] = (size_t)m.nlev * 4;
-    sz[R_FLEV] = (size_t)m.nlev * 8;
-    sz[R_TREE] = (size_t)m.P * 8;
-    sz[R_PA] = sz[R_PB] = sz[R_OA] = sz[R_OB] = sz[R_PD] = sz[R_PC2] = sz[R_PCL] =
-        (size_t)m.nblk * 8;
-    sz[R_JB] = (size_t)m.N;
-    sz[R_BETA] = (size_t)(m.n_steps + 1) * 8;
-    sz[R_DBETA] = sz[R_Q] = (size_t)m.n_steps * 8;
-    sz[R_THR] = (size_t)m.n_steps * 16;
-    sz[R_THETA] = (size_t)m.n_steps * 4;
-    sz[R_ST] = sizeof(DevState);
-    sz[R_TRACE] = (size_t)(m.n_steps + 1) * sizeof(TraceRow);
+// geometry and sizes of each run; couplings are filled by fill_couplings
+bool make_runs(const pa_run_spec* specs, int M, int method, std::vector<RunHost>* out, int* d) {
+    if (!specs || M < 1 || M > (1 << 20) || method < 0 || method > 4) return false;
+    out->clear();
+    for (int m = 0; m < M; ++m) {
+        const pa_run_spec& s = specs[m];
+        long long N;
+        if (!check_lattice(&s.lattice, &N)) return false;
+        if (m == 0) *d = s.lattice.dim;
+        if (s.lattice.dim != *d) return false;
+        if (s.R == 0 || s.ensemble < 0) return false;
+        if (s.couplings.kind < 0 || s.couplings.kind > 2) return false;
+        if ((s.couplings.kind == PA_COUPLING_FERRO) !=
+            (specs[0].couplings.kind == PA_COUPLING_FERRO))
+            return false;
+        if (s.couplings.kind == PA_COUPLING_EXPLICIT && !s.couplings.J) return false;
+        RunHost h;
+        h.L = s.lattice.L;
+        h.N = (int)N;
+        h.W = (int)((N + 31) / 32);
+        h.Wp = (h.W + 3) & ~3;
+        h.nlev = (int)(*d * N / 2 + 1);
+        h.P = 1;
+        while (h.P < h.nlev) h.P <<= 1;
+        h.R = s.R;
+        h.Rcap = s.R_cap ? s.R_cap : default_cap(s.R, method);
+        if (h.Rcap < h.R || h.Rcap > (1u << 30)) return false;
+        h.nblk = (int)((h.Rcap + SCAN_CHUNK - 1) / SCAN_CHUNK);
+        h.ngrp = (int)((h.Rcap + 31) / 32);
+        h.ensemble = s.ensemble;
+        h.parity = 0;
+        out->push_back(std::move(h));
+    }
+    return true;
+}
+
+Layout make_layout(const std::vector<RunHost>& runs, int n_steps) {
     Layout L;
+    size_t nblk = 0, ngrp = 0;
+    for (const RunHost& h : runs) {
+        nblk += h.nblk;
+        ngrp += h.ngrp;
+    }
+    const size_t M = runs.size();
+    size_t sz[S_COUNT];
+    sz[S_RUNS] = M * sizeof(RunDesc);
+    sz[S_B2R] = nblk * 4;
+    sz[S_G2R] = ngrp * 4;
+    sz[S_BETA] = (size_t)(n_steps + 1) * 8;
+    sz[S_DBETA] = sz[S_Q] = (size_t)n_steps * 8;
+    sz[S_THR] = (size_t)n_steps * 16;
+    sz[S_THETA] = (size_t)n_steps * 4;
+    sz[S_IDS] = M * 4;
+    sz[S_WOUT] = (size_t)(n_steps + 1) * sizeof(pa_weighted_obs);
     size_t o = 0;
-    for (int r = 0; r < R_COUNT; ++r) {
-        L.off[r] = o;
+    for (int r = 0; r < S_COUNT; ++r) {
+        L.shared_off[r] = o;
         o += align256(sz[r]);
+    }
+    for (const RunHost& h : runs) {
+        std::array<size_t, R_COUNT> off;
+        size_t rs[R_COUNT];
+        const size_t rows = h.Rcap;
+        rs[R_SPIN0] = rs[R_SPIN1] = rows * h.Wp * 4;
+        rs[R_E0] = rs[R_E1] = rs[R_F0] = rs[R_F1] = rs[R_M] = rs[R_ANC] = rs[R_CNT] = rows * 4;
+        rs[R_C] = rs[R_G] = rows * 8;
+        rs[R_HIST] = (size_t)h.nlev * 4;
+        rs[R_FLEV] = (size_t)h.nlev * 8;
+        rs[R_TREE] = (size_t)h.P * 8;
+        rs[R_PA] = rs[R_PB] = rs[R_OA] = rs[R_OB] = rs[R_PD] = rs[R_PCL] = (size_t)h.nblk * 8;
+        rs[R_JB] = (size_t)h.N;
+        rs[R_ST] = sizeof(DevState);
+        rs[R_TRACE] = (size_t)(n_steps + 1) * sizeof(TraceRow);
+        for (int r = 0; r < R_COUNT; ++r) {
+            off[r] = o;
+            o += align256(rs[r]);
+        }
+        L.run_off.push_back(off);
     }
     L.total = o;
     return L;
@@ -131,6 +192,36 @@ bool make_magic(int L, int N, uint32_t* m_out, uint32_t* sh_out) {
     return false;
 }
 
+// couplings: bit a of byte s is set when the bond (s, s + e_a) has J = -1
+bool fill_couplings(RunHost& h, int d, const pa_couplings& cpl) {
+    h.jb.assign((size_t)h.N, 0);
+    int nneg = 0;
+    if (cpl.kind == PA_COUPLING_EA_PM) {
+        const uint32_t dk0 = (uint32_t)(cpl.disorder_seed & 0xFFFFFFFFu);
+        const uint32_t dk1 = (uint32_t)(cpl.disorder_seed >> 32);
+        for (int b = 0; b < d * h.N; ++b) {
+            const uint4x x =
+                philox((uint32_t)(b >> 7), DOM_DISORDER, 0u, cpl.realization, dk0, dk1);
+            const uint32_t lanes[4] = {x.x, x.y, x.z, x.w};
+            if ((lanes[(b >> 5) & 3] >> (b & 31)) & 1u) {
+                h.jb[b % h.N] |= (uint8_t)(1u << (b / h.N));
+                ++nneg;
+            }
+        }
+    } else if (cpl.kind == PA_COUPLING_EXPLICIT) {
+        for (int b = 0; b < d * h.N; ++b) {
+            const int8_t j = cpl.J[b];
+            if (j != 1 && j != -1) return false;
+            if (j == -1) {
+                h.jb[b % h.N] |= (uint8_t)(1u << (b / h.N));
+                ++nneg;
+            }
+        }
+    }
+    h.parity = nneg & 1;
+    return true;
+}
+
 pa_status map_dev_status(int s) {
     switch (s) {
         case S_OK: return PA_OK;
@@ -141,31 +232,31 @@ pa_status map_dev_status(int s) {
     }
 }
 
-#define PA_CUDA(call)                                  \
-    do {                                               \
-        cudaError_t e_ = (call);                       \
-        if (e_ != cudaSuccess) {                       \
-            ctx->sticky = PA_ERR_CUDA;                 \
-            return PA_ERR_CUDA;                        \
-        }                                              \
+#define PA_CUDA(call)                  \
+    do {                               \
+        cudaError_t e_ = (call);       \
+        if (e_ != cudaSuccess) {       \
+            ctx->sticky = PA_ERR_CUDA; \
+            return PA_ERR_CUDA;        \
+        }                              \
     } while (0)
 
-pa_status read_state(pa_ctx* ctx, DevState* st) {
+pa_status read_state(pa_ctx* ctx, int run, DevState* st) {
     PA_CUDA(cudaStreamSynchronize(ctx->stream));
-    PA_CUDA(cudaMemcpy(st, ctx->kp.st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    PA_CUDA(cudaMemcpy(st, ctx->desc[run].st, sizeof(DevState), cudaMemcpyDeviceToHost));
     return PA_OK;
 }
 
 pa_status enqueue_measure(pa_ctx* ctx) {
-    PA_CUDA(launch_measure(ctx->kp, 1, ctx->threads, ctx->stream));
+    PA_CUDA(launch_measure(ctx->kp, ctx->threads, ctx->stream));
     ctx->launches += 1;
     PA_CUDA(launch_family_finish(ctx->kp, 1, ctx->stream, &ctx->launches));
     return PA_OK;
 }
 
-void fill_obs(const pa_ctx* ctx, const TraceRow& t, int step, pa_obs* o) {
+void fill_obs(const pa_ctx* ctx, int run, const TraceRow& t, int step, pa_obs* o) {
     std::memset(o, 0, sizeof(*o));
-    const double N = ctx->N;
+    const double N = ctx->runs[run].N;
     o->step = step;
     o->R_i = t.R_i;
     o->R_prev = t.R_prev;
@@ -192,78 +283,114 @@ void fill_obs(const pa_ctx* ctx, const TraceRow& t, int step, pa_obs* o) {
     o->accept_rate = th > 0 ? (double)o->accepts / (th * N * R) : 0.0;
 }
 
+// all kernels of one temperature step
+pa_status enqueue_step(pa_ctx* ctx, int64_t* launches) {
+    PA_CUDA(launch_resample(ctx->kp, ctx->stream, launches));
+    PA_CUDA(launch_sweep(ctx->kp, ctx->threads, ctx->stream));
+    if (launches) *launches += 1;
+    PA_CUDA(launch_family_finish(ctx->kp, 0, ctx->stream, launches));
+    return PA_OK;
+}
+
+// capture one temperature step; every kernel reads the step index and the
+// population sizes from device memory, so the same graph serves every step
+pa_status build_graph(pa_ctx* ctx) {
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    PA_CUDA(prepare_sweep(ctx->kp, ctx->threads));
+    cudaGraph_t g = nullptr;
+    PA_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int64_t n = 0;
+    const pa_status s = enqueue_step(ctx, &n);
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (s != PA_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) {
+        ctx->sticky = PA_ERR_CUDA;
+        return PA_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        ctx->graph = nullptr;
+        ctx->sticky = PA_ERR_CUDA;
+        return PA_ERR_CUDA;
+    }
+    ctx->graph_threads = ctx->threads;
+    ctx->graph_kernels = n;
+    return PA_OK;
+}
+
+bool valid_schedule(const pa_schedule* sched) {
+    if (!sched || !sched->beta || !sched->theta || sched->n_steps < 1) return false;
+    const int n = sched->n_steps;
+    if (sched->beta[0] != 0.0) return false;
+    for (int i = 1; i <= n; ++i)
+        if (!(sched->beta[i] > sched->beta[i - 1]) || !std::isfinite(sched->beta[i])) return false;
+    for (int i = 0; i < n; ++i)
+        if (sched->theta[i] >= (1u << 24)) return false;
+    return true;
+}
+
+bool valid_run(const pa_ctx* ctx, int run) { return ctx && run >= 0 && run < ctx->M; }
+
 }  // namespace
 
 extern "C" {
 
-size_t pa_workspace_bytes(const pa_lattice* lat, uint32_t R, uint32_t R_cap, int32_t n_steps,
-                          pa_resampler resampler) {
-    Dims m;
-    if (!make_dims(lat, R, R_cap, n_steps, (int)resampler, &m)) return 0;
-    return make_layout(m).total;
+size_t pa_batch_workspace_bytes(const pa_run_spec* runs, int32_t M, int32_t n_steps,
+                                pa_resampler resampler) {
+    std::vector<RunHost> rh;
+    int d = 0;
+    if (n_steps < 1 || !make_runs(runs, M, (int)resampler, &rh, &d)) return 0;
+    return make_layout(rh, n_steps).total;
 }
 
-pa_status pa_init(pa_ctx** out, const pa_lattice* lat, const pa_couplings* cpl, uint32_t R,
-                  uint32_t R_cap, const pa_schedule* sched, pa_resampler resampler, uint64_t seed,
-                  void* cuda_stream, void* workspace, size_t workspace_bytes) {
-    if (!out || !cpl || !sched || !sched->beta || !sched->theta) return PA_ERR_ARG;
-    *out = nullptr;
-    Dims m;
-    if (!make_dims(lat, R, R_cap, sched->n_steps, (int)resampler, &m)) return PA_ERR_ARG;
-    const int n = sched->n_steps;
-    if (sched->beta[0] != 0.0) return PA_ERR_ARG;
-    for (int i = 1; i <= n; ++i)
-        if (!(sched->beta[i] > sched->beta[i - 1]) || !std::isfinite(sched->beta[i]))
-            return PA_ERR_ARG;
-    for (int i = 0; i < n; ++i)
-        if (sched->theta[i] >= (1u << 24)) return PA_ERR_ARG;
-    if (cpl->kind < 0 || cpl->kind > 2) return PA_ERR_ARG;
-    if (cpl->kind == PA_COUPLING_EXPLICIT && !cpl->J) return PA_ERR_ARG;
+size_t pa_workspace_bytes(const pa_lattice* lat, uint32_t R, uint32_t R_cap, int32_t n_steps,
+                          pa_resampler resampler) {
+    if (!lat) return 0;
+    pa_run_spec s;
+    std::memset(&s, 0, sizeof(s));
+    s.lattice = *lat;
+    s.couplings.kind = PA_COUPLING_FERRO;
+    s.R = R;
+    s.R_cap = R_cap;
+    return pa_batch_workspace_bytes(&s, 1, n_steps, resampler);
+}
 
-    // couplings: bit a of byte s is set when the bond (s, s + e_a) has J = -1
-    std::vector<uint8_t> jb((size_t)m.N, 0);
-    int nneg = 0;
-    if (cpl->kind == PA_COUPLING_EA_PM) {
-        const uint32_t dk0 = (uint32_t)(cpl->disorder_seed & 0xFFFFFFFFu);
-        const uint32_t dk1 = (uint32_t)(cpl->disorder_seed >> 32);
-        for (int b = 0; b < m.d * m.N; ++b) {
-            const uint4x x = philox((uint32_t)(b >> 7), DOM_DISORDER, 0u, cpl->realization, dk0, dk1);
-            const uint32_t lanes[4] = {x.x, x.y, x.z, x.w};
-            const uint32_t bit = (lanes[(b >> 5) & 3] >> (b & 31)) & 1u;
-            if (bit) {
-                jb[b % m.N] |= (uint8_t)(1u << (b / m.N));
-                ++nneg;
-            }
-        }
-    } else if (cpl->kind == PA_COUPLING_EXPLICIT) {
-        for (int b = 0; b < m.d * m.N; ++b) {
-            const int8_t j = cpl->J[b];
-            if (j != 1 && j != -1) return PA_ERR_ARG;
-            if (j == -1) {
-                jb[b % m.N] |= (uint8_t)(1u << (b / m.N));
-                ++nneg;
-            }
-        }
-    }
+pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
+                        const pa_schedule* sched, pa_resampler resampler, uint64_t seed,
+                        void* cuda_stream, void* workspace, size_t workspace_bytes) {
+    if (!out) return PA_ERR_ARG;
+    *out = nullptr;
+    if (!valid_schedule(sched)) return PA_ERR_ARG;
+    std::vector<RunHost> rh;
+    int d = 0;
+    if (!make_runs(specs, M, (int)resampler, &rh, &d)) return PA_ERR_ARG;
+    for (int m = 0; m < M; ++m)
+        if (!fill_couplings(rh[m], d, specs[m].couplings)) return PA_ERR_ARG;
+    const int n = sched->n_steps;
 
     pa_ctx* ctx = new (std::nothrow) pa_ctx();
     if (!ctx) return PA_ERR_NOMEM;
-    ctx->d = m.d;
-    ctx->L = m.L;
-    ctx->N = m.N;
-    ctx->W = m.W;
-    ctx->Wp = m.Wp;
-    ctx->R = m.R;
-    ctx->Rcap = m.Rcap;
+    ctx->d = d;
+    ctx->M = M;
     ctx->n_steps = n;
     ctx->method = (int)resampler;
     ctx->seed = seed;
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->beta.assign(sched->beta, sched->beta + n + 1);
     ctx->theta.assign(sched->theta, sched->theta + n);
-    ctx->threads = sweep_threads(m.N);
+    int maxN = 0;
+    for (const RunHost& h : rh) maxN = h.N > maxN ? h.N : maxN;
+    ctx->threads = sweep_threads(maxN);
+    ctx->runs = std::move(rh);
 
-    const Layout lay = make_layout(m);
+    const Layout lay = make_layout(ctx->runs, n);
     if (workspace) {
         if (workspace_bytes < lay.total || ((uintptr_t)workspace & 255u)) {
             delete ctx;
@@ -281,60 +408,88 @@ pa_status pa_init(pa_ctx** out, const pa_lattice* lat, const pa_couplings* cpl, 
         ctx->owns = true;
     }
     char* base = (char*)ctx->ws;
+
+    // batch-wide parameters
     KParams& p = ctx->kp;
     std::memset(&p, 0, sizeof(p));
-    p.d = m.d;
-    p.L = m.L;
-    p.N = m.N;
-    p.W = m.W;
-    p.Wp = m.Wp;
-    p.nlev = m.nlev;
-    p.parity = nneg & 1;
-    p.ea = cpl->kind != PA_COUPLING_FERRO;
-    p.R = m.R;
-    p.Rcap = m.Rcap;
-    p.n_steps = n;
+    p.d = d;
+    p.ea = specs[0].couplings.kind != PA_COUPLING_FERRO;
     p.method = (int)resampler;
+    p.n_steps = n;
+    p.M = M;
+    p.maxN = maxN;
     p.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
     p.k1 = (uint32_t)(seed >> 32);
     for (int r = 0; r < 10; ++r) {
         p.rk0[r] = p.k0 + (uint32_t)r * PHILOX_W0;
         p.rk1[r] = p.k1 + (uint32_t)r * PHILOX_W1;
     }
-    if (!make_magic(m.L, m.N, &p.magicL, &p.shiftL)) {
-        pa_destroy(ctx);
-        return PA_ERR_ARG;
+    p.runs = (const RunDesc*)(base + lay.shared_off[S_RUNS]);
+    p.blk2run = (const uint32_t*)(base + lay.shared_off[S_B2R]);
+    p.grp2run = (const uint32_t*)(base + lay.shared_off[S_G2R]);
+    p.beta = (const double*)(base + lay.shared_off[S_BETA]);
+    p.dbeta = (const double*)(base + lay.shared_off[S_DBETA]);
+    p.q = (const double*)(base + lay.shared_off[S_Q]);
+    p.thr = (const uint32_t*)(base + lay.shared_off[S_THR]);
+    p.theta = (const uint32_t*)(base + lay.shared_off[S_THETA]);
+    ctx->d_ids = (int32_t*)(base + lay.shared_off[S_IDS]);
+    ctx->d_wout = (pa_weighted_obs*)(base + lay.shared_off[S_WOUT]);
+
+    // per-run descriptors and block -> run maps
+    std::vector<uint32_t> b2r, g2r;
+    ctx->desc.resize(M);
+    uint32_t blk0 = 0, grp0 = 0;
+    for (int m = 0; m < M; ++m) {
+        const RunHost& h = ctx->runs[m];
+        const auto& off = lay.run_off[m];
+        RunDesc& r = ctx->desc[m];
+        std::memset(&r, 0, sizeof(r));
+        r.L = h.L;
+        r.N = h.N;
+        r.W = h.W;
+        r.Wp = h.Wp;
+        r.nlev = h.nlev;
+        r.parity = h.parity;
+        r.R = h.R;
+        r.Rcap = h.Rcap;
+        if (!make_magic(h.L, h.N, &r.magicL, &r.shiftL)) {
+            pa_destroy(ctx);
+            return PA_ERR_ARG;
+        }
+        r.nblk = h.nblk;
+        r.blk0 = blk0;
+        r.grp0 = grp0;
+        r.run = (uint32_t)m;
+        for (int b = 0; b < h.nblk; ++b) b2r.push_back((uint32_t)m);
+        for (int g = 0; g < h.ngrp; ++g) g2r.push_back((uint32_t)m);
+        blk0 += h.nblk;
+        grp0 += h.ngrp;
+        r.spins[0] = (uint32_t*)(base + off[R_SPIN0]);
+        r.spins[1] = (uint32_t*)(base + off[R_SPIN1]);
+        r.E[0] = (int32_t*)(base + off[R_E0]);
+        r.E[1] = (int32_t*)(base + off[R_E1]);
+        r.fam[0] = (uint32_t*)(base + off[R_F0]);
+        r.fam[1] = (uint32_t*)(base + off[R_F1]);
+        r.M = (int32_t*)(base + off[R_M]);
+        r.anc = (uint32_t*)(base + off[R_ANC]);
+        r.counts = (uint32_t*)(base + off[R_CNT]);
+        r.C = (uint64_t*)(base + off[R_C]);
+        r.G = (uint64_t*)(base + off[R_G]);
+        r.hist = (uint32_t*)(base + off[R_HIST]);
+        r.flev = (uint64_t*)(base + off[R_FLEV]);
+        r.tree = (double*)(base + off[R_TREE]);
+        r.partA = (uint64_t*)(base + off[R_PA]);
+        r.partB = (uint64_t*)(base + off[R_PB]);
+        r.offA = (uint64_t*)(base + off[R_OA]);
+        r.offB = (uint64_t*)(base + off[R_OB]);
+        r.partD = (double*)(base + off[R_PD]);
+        r.partCL = (double*)(base + off[R_PCL]);
+        r.jbits = (const uint8_t*)(base + off[R_JB]);
+        r.st = (DevState*)(base + off[R_ST]);
+        r.trace = (TraceRow*)(base + off[R_TRACE]);
     }
-    p.nblk = m.nblk;
-    p.spins[0] = (uint32_t*)(base + lay.off[R_SPIN0]);
-    p.spins[1] = (uint32_t*)(base + lay.off[R_SPIN1]);
-    p.E[0] = (int32_t*)(base + lay.off[R_E0]);
-    p.E[1] = (int32_t*)(base + lay.off[R_E1]);
-    p.fam[0] = (uint32_t*)(base + lay.off[R_F0]);
-    p.fam[1] = (uint32_t*)(base + lay.off[R_F1]);
-    p.M = (int32_t*)(base + lay.off[R_M]);
-    p.anc = (uint32_t*)(base + lay.off[R_ANC]);
-    p.counts = (uint32_t*)(base + lay.off[R_CNT]);
-    p.C = (uint64_t*)(base + lay.off[R_C]);
-    p.G = (uint64_t*)(base + lay.off[R_G]);
-    p.hist = (uint32_t*)(base + lay.off[R_HIST]);
-    p.flev = (uint64_t*)(base + lay.off[R_FLEV]);
-    p.tree = (double*)(base + lay.off[R_TREE]);
-    p.partA = (uint64_t*)(base + lay.off[R_PA]);
-    p.partB = (uint64_t*)(base + lay.off[R_PB]);
-    p.offA = (uint64_t*)(base + lay.off[R_OA]);
-    p.offB = (uint64_t*)(base + lay.off[R_OB]);
-    p.partD = (double*)(base + lay.off[R_PD]);
-    p.partC2 = (unsigned long long*)(base + lay.off[R_PC2]);
-    p.partCL = (double*)(base + lay.off[R_PCL]);
-    p.jbits = (const uint8_t*)(base + lay.off[R_JB]);
-    p.beta = (const double*)(base + lay.off[R_BETA]);
-    p.dbeta = (const double*)(base + lay.off[R_DBETA]);
-    p.q = (const double*)(base + lay.off[R_Q]);
-    p.thr = (const uint32_t*)(base + lay.off[R_THR]);
-    p.theta = (const uint32_t*)(base + lay.off[R_THETA]);
-    p.st = (DevState*)(base + lay.off[R_ST]);
-    p.trace = (TraceRow*)(base + lay.off[R_TRACE]);
+    p.nblk_total = blk0;
+    p.ngrp_total = grp0;
 
     // per-step tables: dbeta, q = exp(-4 dbeta), Metropolis thresholds at beta_i
     std::vector<double> dbeta(n), q(n);
@@ -349,28 +504,36 @@ pa_status pa_init(pa_ctx** out, const pa_lattice* lat, const pa_couplings* cpl, 
             thr[4 * (i - 1) + k] = (t >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)std::floor(t);
         }
     }
-    DevState st0;
-    std::memset(&st0, 0, sizeof(st0));
-    st0.R_cur = m.R;
-    st0.R_prev = m.R;
 
     cudaError_t e = cudaSuccess;
     auto up = [&](const void* dev, const void* host, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMemcpy((void*)dev, host, bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && bytes)
+            e = cudaMemcpy((void*)dev, host, bytes, cudaMemcpyHostToDevice);
     };
-    up(p.jbits, jb.data(), jb.size());
+    up(p.runs, ctx->desc.data(), sizeof(RunDesc) * M);
+    up(p.blk2run, b2r.data(), b2r.size() * 4);
+    up(p.grp2run, g2r.data(), g2r.size() * 4);
     up(p.beta, ctx->beta.data(), sizeof(double) * (n + 1));
     up(p.dbeta, dbeta.data(), sizeof(double) * n);
     up(p.q, q.data(), sizeof(double) * n);
     up(p.thr, thr.data(), sizeof(uint32_t) * 4 * n);
     up(p.theta, ctx->theta.data(), sizeof(uint32_t) * n);
-    up(p.st, &st0, sizeof(st0));
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.hist, 0, (size_t)m.nlev * 4, ctx->stream);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(p.trace, 0, (size_t)(n + 1) * sizeof(TraceRow), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.counts, 0, (size_t)m.Rcap * 4, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.anc, 0, (size_t)m.Rcap * 4, ctx->stream);
-    if (e == cudaSuccess) e = launch_init_spins(p, ctx->stream);
+    for (int m = 0; m < M && e == cudaSuccess; ++m) {
+        const RunHost& h = ctx->runs[m];
+        const RunDesc& r = ctx->desc[m];
+        DevState st0;
+        std::memset(&st0, 0, sizeof(st0));
+        st0.R_cur = h.R;
+        st0.R_prev = h.R;
+        up(r.jbits, h.jb.data(), h.jb.size());
+        up(r.st, &st0, sizeof(st0));
+        if (e == cudaSuccess) e = cudaMemsetAsync(r.hist, 0, (size_t)h.nlev * 4, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(r.trace, 0, (size_t)(n + 1) * sizeof(TraceRow), ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(r.counts, 0, (size_t)h.Rcap * 4, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(r.anc, 0, (size_t)h.Rcap * 4, ctx->stream);
+    }
+    if (e == cudaSuccess) e = launch_init_spins(p, ctx->desc.data(), ctx->stream);
     if (e != cudaSuccess) {
         pa_destroy(ctx);
         return PA_ERR_CUDA;
@@ -386,14 +549,39 @@ pa_status pa_init(pa_ctx** out, const pa_lattice* lat, const pa_couplings* cpl, 
     return PA_OK;
 }
 
+pa_status pa_init(pa_ctx** out, const pa_lattice* lat, const pa_couplings* cpl, uint32_t R,
+                  uint32_t R_cap, const pa_schedule* sched, pa_resampler resampler, uint64_t seed,
+                  void* cuda_stream, void* workspace, size_t workspace_bytes) {
+    if (!out || !lat || !cpl) return PA_ERR_ARG;
+    pa_run_spec s;
+    std::memset(&s, 0, sizeof(s));
+    s.lattice = *lat;
+    s.couplings = *cpl;
+    s.R = R;
+    s.R_cap = R_cap;
+    s.ensemble = 0;
+    return pa_batch_init(out, &s, 1, sched, resampler, seed, cuda_stream, workspace,
+                         workspace_bytes);
+}
+
+int32_t pa_batch_size(const pa_ctx* ctx) { return ctx ? ctx->M : 0; }
+
 pa_status pa_step(pa_ctx* ctx, int32_t n) {
     if (!ctx || n < 0) return PA_ERR_ARG;
     if (ctx->sticky != PA_OK) return PA_ERR_STATE;
     if (ctx->host_step + n > ctx->n_steps) return PA_ERR_DONE;
+    const bool graph = ctx->use_graph && !ctx->timing && ctx->stream != nullptr;
+    if (graph && n > 0 && (!ctx->graph || ctx->graph_threads != ctx->threads)) {
+        const pa_status s = build_graph(ctx);
+        if (s != PA_OK) return s;
+    }
     for (int k = 0; k < n; ++k) {
-        PA_CUDA(launch_resample(ctx->kp, ctx->stream, &ctx->launches));
         const int i = ctx->host_step + 1;
-        if (ctx->timing) {
+        if (graph) {
+            PA_CUDA(cudaGraphLaunch(ctx->graph, ctx->stream));
+            ctx->launches += ctx->graph_kernels;
+        } else if (ctx->timing) {
+            PA_CUDA(launch_resample(ctx->kp, ctx->stream, &ctx->launches));
             cudaEvent_t a, b;
             PA_CUDA(cudaEventCreate(&a));
             PA_CUDA(cudaEventCreate(&b));
@@ -401,11 +589,14 @@ pa_status pa_step(pa_ctx* ctx, int32_t n) {
             ctx->ev_stop.push_back(b);
             ctx->timed_steps.push_back(i);
             PA_CUDA(cudaEventRecord(a, ctx->stream));
+            PA_CUDA(launch_sweep(ctx->kp, ctx->threads, ctx->stream));
+            ctx->launches += 1;
+            PA_CUDA(cudaEventRecord(b, ctx->stream));
+            PA_CUDA(launch_family_finish(ctx->kp, 0, ctx->stream, &ctx->launches));
+        } else {
+            const pa_status s = enqueue_step(ctx, &ctx->launches);
+            if (s != PA_OK) return s;
         }
-        PA_CUDA(launch_sweep(ctx->kp, ctx->threads, ctx->stream));
-        ctx->launches += 1;
-        if (ctx->timing) PA_CUDA(cudaEventRecord(ctx->ev_stop.back(), ctx->stream));
-        PA_CUDA(launch_family_finish(ctx->kp, 0, ctx->stream, &ctx->launches));
         ctx->host_step = i;
     }
     return PA_OK;
@@ -414,69 +605,90 @@ pa_status pa_step(pa_ctx* ctx, int32_t n) {
 pa_status pa_sync(pa_ctx* ctx) {
     if (!ctx) return PA_ERR_ARG;
     if (ctx->sticky != PA_OK) return ctx->sticky;
-    DevState st;
-    pa_status s = read_state(ctx, &st);
-    if (s != PA_OK) return s;
-    s = map_dev_status(st.status);
-    if (s != PA_OK) ctx->sticky = s;
-    return s;
-}
-
-pa_status pa_observables(pa_ctx* ctx, pa_obs* out) {
-    if (!ctx || !out) return PA_ERR_ARG;
-    pa_status s = pa_sync(ctx);
-    if (s != PA_OK) return s;
-    TraceRow t;
-    PA_CUDA(cudaMemcpy(&t, ctx->kp.trace + ctx->host_step, sizeof(t), cudaMemcpyDeviceToHost));
-    fill_obs(ctx, t, ctx->host_step, out);
+    PA_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int m = 0; m < ctx->M; ++m) {
+        DevState st;
+        PA_CUDA(cudaMemcpy(&st, ctx->desc[m].st, sizeof(DevState), cudaMemcpyDeviceToHost));
+        const pa_status s = map_dev_status(st.status);
+        if (s != PA_OK) {
+            ctx->sticky = s;
+            return s;
+        }
+    }
     return PA_OK;
 }
 
-pa_status pa_trace(pa_ctx* ctx, pa_obs* rows, int32_t max_rows, int32_t* n_rows) {
-    if (!ctx || !rows || max_rows < 0) return PA_ERR_ARG;
+pa_status pa_run_observables(pa_ctx* ctx, int32_t run, pa_obs* out) {
+    if (!valid_run(ctx, run) || !out) return PA_ERR_ARG;
+    pa_status s = pa_sync(ctx);
+    if (s != PA_OK) return s;
+    TraceRow t;
+    PA_CUDA(cudaMemcpy(&t, ctx->desc[run].trace + ctx->host_step, sizeof(t),
+                       cudaMemcpyDeviceToHost));
+    fill_obs(ctx, run, t, ctx->host_step, out);
+    return PA_OK;
+}
+
+pa_status pa_observables(pa_ctx* ctx, pa_obs* out) { return pa_run_observables(ctx, 0, out); }
+
+pa_status pa_run_trace(pa_ctx* ctx, int32_t run, pa_obs* rows, int32_t max_rows,
+                       int32_t* n_rows) {
+    if (!valid_run(ctx, run) || !rows || max_rows < 0) return PA_ERR_ARG;
     pa_status s = pa_sync(ctx);
     if (s != PA_OK) return s;
     int n = ctx->host_step + 1;
     if (n > max_rows) n = max_rows;
     std::vector<TraceRow> t((size_t)n);
     if (n > 0)
-        PA_CUDA(cudaMemcpy(t.data(), ctx->kp.trace, sizeof(TraceRow) * n, cudaMemcpyDeviceToHost));
-    for (int i = 0; i < n; ++i) fill_obs(ctx, t[i], i, rows + i);
+        PA_CUDA(cudaMemcpy(t.data(), ctx->desc[run].trace, sizeof(TraceRow) * n,
+                           cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i) fill_obs(ctx, run, t[i], i, rows + i);
     if (n_rows) *n_rows = n;
     return PA_OK;
 }
 
-pa_status pa_free_energy(pa_ctx* ctx, double* minus_beta_F, double* f_per_spin) {
-    if (!ctx) return PA_ERR_ARG;
-    DevState st;
+pa_status pa_trace(pa_ctx* ctx, pa_obs* rows, int32_t max_rows, int32_t* n_rows) {
+    return pa_run_trace(ctx, 0, rows, max_rows, n_rows);
+}
+
+pa_status pa_run_free_energy(pa_ctx* ctx, int32_t run, double* minus_beta_F, double* f_per_spin) {
+    if (!valid_run(ctx, run)) return PA_ERR_ARG;
     pa_status s = pa_sync(ctx);
     if (s != PA_OK) return s;
-    s = read_state(ctx, &st);
+    DevState st;
+    s = read_state(ctx, run, &st);
     if (s != PA_OK) return s;
-    const double mbf = (double)ctx->N * std::log(2.0) + st.sum_lnQ;
+    const double N = ctx->runs[run].N;
+    const double mbf = N * std::log(2.0) + st.sum_lnQ;
     const double b = ctx->beta[ctx->host_step];
     if (minus_beta_F) *minus_beta_F = mbf;
-    if (f_per_spin) *f_per_spin = b > 0 ? -mbf / (b * ctx->N) : NAN;
+    if (f_per_spin) *f_per_spin = b > 0 ? -mbf / (b * N) : NAN;
     return PA_OK;
 }
 
-pa_status pa_get_array(pa_ctx* ctx, pa_array which, void* host, size_t capacity, size_t* n_out) {
-    if (!ctx || !host) return PA_ERR_ARG;
+pa_status pa_free_energy(pa_ctx* ctx, double* minus_beta_F, double* f_per_spin) {
+    return pa_run_free_energy(ctx, 0, minus_beta_F, f_per_spin);
+}
+
+pa_status pa_run_get_array(pa_ctx* ctx, int32_t run, pa_array which, void* host, size_t capacity,
+                           size_t* n_out) {
+    if (!valid_run(ctx, run) || !host) return PA_ERR_ARG;
     pa_status s = pa_sync(ctx);
     if (s != PA_OK) return s;
     DevState st;
-    s = read_state(ctx, &st);
+    s = read_state(ctx, run, &st);
     if (s != PA_OK) return s;
     const int par = ctx->host_step & 1;
-    const KParams& p = ctx->kp;
+    const RunDesc& r = ctx->desc[run];
+    const RunHost& h = ctx->runs[run];
     size_t n = 0;
     switch (which) {
         case PA_ARRAY_SPINS:
-            n = (size_t)st.R_cur * ctx->W;
+            n = (size_t)st.R_cur * h.W;
             if (capacity < n) return PA_ERR_ARG;
             if (st.R_cur)
-                PA_CUDA(cudaMemcpy2D(host, (size_t)ctx->W * 4, p.spins[par], (size_t)ctx->Wp * 4,
-                                     (size_t)ctx->W * 4, st.R_cur, cudaMemcpyDeviceToHost));
+                PA_CUDA(cudaMemcpy2D(host, (size_t)h.W * 4, r.spins[par], (size_t)h.Wp * 4,
+                                     (size_t)h.W * 4, st.R_cur, cudaMemcpyDeviceToHost));
             break;
         case PA_ARRAY_ENERGY:
         case PA_ARRAY_FAMILY:
@@ -484,17 +696,17 @@ pa_status pa_get_array(pa_ctx* ctx, pa_array which, void* host, size_t capacity,
         case PA_ARRAY_MAGNET: {
             n = st.R_cur;
             if (capacity < n) return PA_ERR_ARG;
-            const void* src = which == PA_ARRAY_ENERGY   ? (const void*)p.E[par]
-                              : which == PA_ARRAY_FAMILY ? (const void*)p.fam[par]
-                              : which == PA_ARRAY_MAGNET ? (const void*)p.M
-                                                         : (const void*)p.anc;
+            const void* src = which == PA_ARRAY_ENERGY   ? (const void*)r.E[par]
+                              : which == PA_ARRAY_FAMILY ? (const void*)r.fam[par]
+                              : which == PA_ARRAY_MAGNET ? (const void*)r.M
+                                                         : (const void*)r.anc;
             if (n) PA_CUDA(cudaMemcpy(host, src, n * 4, cudaMemcpyDeviceToHost));
             break;
         }
         case PA_ARRAY_COUNTS:
             n = ctx->host_step > 0 ? st.R_prev : 0;
             if (capacity < n) return PA_ERR_ARG;
-            if (n) PA_CUDA(cudaMemcpy(host, p.counts, n * 4, cudaMemcpyDeviceToHost));
+            if (n) PA_CUDA(cudaMemcpy(host, r.counts, n * 4, cudaMemcpyDeviceToHost));
             break;
         default:
             return PA_ERR_ARG;
@@ -503,41 +715,79 @@ pa_status pa_get_array(pa_ctx* ctx, pa_array which, void* host, size_t capacity,
     return PA_OK;
 }
 
+pa_status pa_get_array(pa_ctx* ctx, pa_array which, void* host, size_t capacity, size_t* n_out) {
+    return pa_run_get_array(ctx, 0, which, host, capacity, n_out);
+}
+
 pa_status pa_set_state(pa_ctx* ctx, const uint32_t* spins, const uint32_t* family, uint32_t R_i,
                        int32_t step, double sum_lnQ) {
-    if (!ctx || !spins || R_i == 0 || R_i > ctx->Rcap || step < 0 || step > ctx->n_steps)
+    if (!ctx || ctx->M != 1 || !spins || R_i == 0 || R_i > ctx->runs[0].Rcap || step < 0 ||
+        step > ctx->n_steps)
         return PA_ERR_ARG;
     if (ctx->sticky != PA_OK) return PA_ERR_STATE;
-    const KParams& p = ctx->kp;
+    const RunDesc& r = ctx->desc[0];
+    const RunHost& h = ctx->runs[0];
     const int par = step & 1;
     std::vector<uint32_t> fam((size_t)R_i);
     for (uint32_t j = 0; j < R_i; ++j) {
         fam[j] = family ? family[j] : j;
-        if (fam[j] >= ctx->R) return PA_ERR_ARG;
+        if (fam[j] >= h.R) return PA_ERR_ARG;
         if (j > 0 && fam[j] < fam[j - 1]) return PA_ERR_ARG;  // families stay sorted by slot
     }
     PA_CUDA(cudaStreamSynchronize(ctx->stream));
-    PA_CUDA(cudaMemset(p.spins[par], 0, (size_t)R_i * ctx->Wp * 4));
-    PA_CUDA(cudaMemcpy2D(p.spins[par], (size_t)ctx->Wp * 4, spins, (size_t)ctx->W * 4,
-                         (size_t)ctx->W * 4, R_i, cudaMemcpyHostToDevice));
-    PA_CUDA(cudaMemcpy(p.fam[par], fam.data(), (size_t)R_i * 4, cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemset(r.spins[par], 0, (size_t)R_i * h.Wp * 4));
+    PA_CUDA(cudaMemcpy2D(r.spins[par], (size_t)h.Wp * 4, spins, (size_t)h.W * 4, (size_t)h.W * 4,
+                         R_i, cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(r.fam[par], fam.data(), (size_t)R_i * 4, cudaMemcpyHostToDevice));
     DevState st;
     std::memset(&st, 0, sizeof(st));
     st.step = step;
     st.R_cur = R_i;
     st.R_prev = R_i;
     st.sum_lnQ = sum_lnQ;
-    PA_CUDA(cudaMemcpy(p.st, &st, sizeof(st), cudaMemcpyHostToDevice));
-    PA_CUDA(cudaMemset(p.hist, 0, (size_t)p.nlev * 4));
+    PA_CUDA(cudaMemcpy(r.st, &st, sizeof(st), cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemset(r.hist, 0, (size_t)h.nlev * 4));
     TraceRow t;
     std::memset(&t, 0, sizeof(t));
     t.sum_lnQ = sum_lnQ;
     t.R_prev = R_i;
-    PA_CUDA(cudaMemcpy(p.trace + step, &t, sizeof(t), cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(r.trace + step, &t, sizeof(t), cudaMemcpyHostToDevice));
     ctx->host_step = step;
-    pa_status s = enqueue_measure(ctx);
+    const pa_status s = enqueue_measure(ctx);
     if (s != PA_OK) return s;
     return pa_sync(ctx);
+}
+
+pa_status pa_weighted(pa_ctx* ctx, int32_t ensemble, pa_weighted_obs* rows, int32_t max_rows,
+                      int32_t* n_rows) {
+    if (!ctx || !rows || max_rows < 0) return PA_ERR_ARG;
+    std::vector<int32_t> ids;
+    for (int m = 0; m < ctx->M; ++m)
+        if (ctx->runs[m].ensemble == ensemble) ids.push_back(m);
+    if (ids.empty()) return PA_ERR_ARG;
+    for (int32_t m : ids)
+        if (ctx->runs[m].N != ctx->runs[ids[0]].N) return PA_ERR_ARG;
+    pa_status s = pa_sync(ctx);
+    if (s != PA_OK) return s;
+    int n = ctx->host_step + 1;
+    if (n > max_rows) n = max_rows;
+    if (n > 0) {
+        PA_CUDA(cudaMemcpy(ctx->d_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice));
+        PA_CUDA(launch_weighted(ctx->kp, ctx->d_ids, (int)ids.size(), n, ctx->d_wout,
+                                ctx->stream));
+        ctx->launches += 1;
+        PA_CUDA(cudaStreamSynchronize(ctx->stream));
+        PA_CUDA(cudaMemcpy(rows, ctx->d_wout, sizeof(pa_weighted_obs) * n,
+                           cudaMemcpyDeviceToHost));
+    }
+    if (n_rows) *n_rows = n;
+    return PA_OK;
+}
+
+pa_status pa_set_graph(pa_ctx* ctx, int32_t on) {
+    if (!ctx) return PA_ERR_ARG;
+    ctx->use_graph = on != 0;
+    return PA_OK;
 }
 
 pa_status pa_enable_timing(pa_ctx* ctx, int32_t on) {
@@ -551,15 +801,19 @@ pa_status pa_sweep_timing(pa_ctx* ctx, double* ms, int64_t* launches, double* up
     pa_status s = pa_sync(ctx);
     if (s != PA_OK) return s;
     double total = 0.0, upd = 0.0;
-    std::vector<TraceRow> t((size_t)ctx->n_steps + 1);
-    PA_CUDA(cudaMemcpy(t.data(), ctx->kp.trace, sizeof(TraceRow) * t.size(),
-                       cudaMemcpyDeviceToHost));
+    std::vector<std::vector<TraceRow>> t((size_t)ctx->M);
+    for (int m = 0; m < ctx->M; ++m) {
+        t[m].resize((size_t)ctx->n_steps + 1);
+        PA_CUDA(cudaMemcpy(t[m].data(), ctx->desc[m].trace, sizeof(TraceRow) * t[m].size(),
+                           cudaMemcpyDeviceToHost));
+    }
     for (size_t k = 0; k < ctx->ev_start.size(); ++k) {
         float f = 0.f;
         PA_CUDA(cudaEventElapsedTime(&f, ctx->ev_start[k], ctx->ev_stop[k]));
         total += f;
         const int i = ctx->timed_steps[k];
-        upd += (double)ctx->theta[i - 1] * (double)ctx->N * (double)t[i].R_i;
+        for (int m = 0; m < ctx->M; ++m)
+            upd += (double)ctx->theta[i - 1] * (double)ctx->runs[m].N * (double)t[m][i].R_i;
         cudaEventDestroy(ctx->ev_start[k]);
         cudaEventDestroy(ctx->ev_stop[k]);
     }
@@ -588,6 +842,7 @@ pa_status pa_destroy(pa_ctx* ctx) {
         cudaEventDestroy(ctx->ev_start[k]);
         cudaEventDestroy(ctx->ev_stop[k]);
     }
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->owns && ctx->ws) cudaFree(ctx->ws);
     delete ctx;
     return PA_OK;

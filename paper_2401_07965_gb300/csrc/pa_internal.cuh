@@ -1,13 +1,20 @@
 // pa_internal.cuh -- device-side definitions shared by the library's kernels.
 //
+// A context advances a batch of M >= 1 independent runs (same dimension,
+// coupling kind, rule and schedule; lattice size, population size, couplings
+// and seed-independent identity per run) with the same kernels: one launch per
+// phase covers every run.
+//
 // Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), keyed
-// by the 64-bit run seed; the counter (c0, c1, c2, c3) carries the draw's
-// purpose in the top nibble of c1:
-//   sweep      c0 = slot >> 5, c1 = (sweep << 4) | (colour << 3) | plane block,
-//              c2 = step, c3 = site
-//   init       c0 = word >> 2, c1 = 1 << 28,             c2 = 0,    c3 = replica
-//   resample   c0 = index,     c1 = (2 << 28) | rule,    c2 = step, c3 = chunk
-//   disorder   c0 = bond >> 7, c1 = 3 << 28,             c2 = 0,    c3 = realization
+// by the 64-bit seed of the context; the counter (c0, c1, c2, c3) carries the
+// draw's purpose in the top nibble of c1 and the run's identity:
+//   sweep      c0 = global replica group (slot_base + slot) >> 5,
+//              c1 = (sweep << 4) | (colour << 3) | plane block, c2 = step, c3 = site
+//   init       c0 = word >> 2, c1 = 1 << 28, c2 = 0, c3 = slot_base + replica
+//   resample   c0 = index, c1 = (2 << 28) | (run << 8) | rule, c2 = step, c3 = chunk
+//   disorder   c0 = bond >> 7, c1 = 3 << 28, c2 = 0, c3 = realization
+// slot_base of run m is 32 x (the sweep CTAs of runs 0..m-1); a batch of one
+// run has slot_base 0 and run index 0.
 #pragma once
 
 #include <cstdint>
@@ -90,26 +97,25 @@ struct TraceRow {
     uint64_t pad;
 };
 
-// Everything a kernel needs, passed by value.
-struct KParams {
-    int d, L, N, W, Wp;      // lattice; W words per replica, Wp padded to 4
+// Per-run description, in device memory (one per run of the batch).
+struct RunDesc {
+    int L, N, W, Wp;         // lattice; W words per replica, Wp padded to 4
     int nlev;                // d*N/2 + 1 histogram levels (level = U >> 1)
     int parity;              // U mod 2, the same for every configuration
-    int ea;                  // couplings present
     uint32_t R, Rcap;
-    int n_steps, method;
-    uint32_t k0, k1;         // Philox key = seed
-    uint32_t rk0[10], rk1[10];  // its round keys k + r*W (round r = 0..9)
     uint32_t magicL, shiftL; // fast division by L
-    int nblk;                // blocks of the scan kernels
+    int nblk;                // scan blocks of this run
+    uint32_t blk0;           // its first block in the flattened scan grids
+    uint32_t grp0;           // its first CTA in the flattened sweep grid (= slot_base / 32)
+    uint32_t run;            // run index
     uint32_t* spins[2];
     int32_t* E[2];
     uint32_t* fam[2];
     int32_t* M;
     uint32_t* anc;
     uint32_t* counts;
-    uint64_t* C;             // inclusive prefix of f (or of remainders, residual)
-    uint64_t* G;
+    uint64_t* C;             // inclusive prefix of f
+    uint64_t* G;             // inclusive prefix of the remainders (residual rule)
     uint32_t* hist;          // level histogram of the current population
     uint64_t* flev;          // fixed-point tau-hat per level
     double* tree;            // pairwise-sum scratch (power of two >= nlev)
@@ -118,16 +124,28 @@ struct KParams {
     uint64_t* offA;          // per-block exclusive offsets
     uint64_t* offB;
     double* partD;
-    unsigned long long* partC2;
     double* partCL;
     const uint8_t* jbits;    // bit a of byte s: bond (s, s+e_a) has J = -1
+    DevState* st;
+    TraceRow* trace;         // n_steps + 1 rows
+};
+
+// Batch-wide parameters, passed by value to every kernel.
+struct KParams {
+    int d, ea, method, n_steps, M;
+    int maxN;                // largest lattice of the batch
+    uint32_t k0, k1;         // Philox key = seed
+    uint32_t rk0[10], rk1[10];  // its round keys k + r*W (round r = 0..9)
+    uint32_t nblk_total;     // flattened scan grid
+    uint32_t ngrp_total;     // flattened sweep grid
+    const RunDesc* runs;
+    const uint32_t* blk2run; // scan block -> run
+    const uint32_t* grp2run; // sweep CTA -> run
     const double* beta;      // n_steps + 1
     const double* dbeta;     // n_steps
     const double* q;         // exp(-4 dbeta), n_steps
     const uint32_t* thr;     // 4 per step (index 1..d used)
     const uint32_t* theta;   // n_steps
-    DevState* st;
-    TraceRow* trace;         // n_steps + 1 rows
 };
 
 constexpr int SCAN_THREADS = 256;
@@ -138,11 +156,12 @@ constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
 
 // kernel launchers (defined in the .cu files)
 namespace pa {
-cudaError_t launch_init_spins(const KParams& p, cudaStream_t s);
-cudaError_t launch_measure(const KParams& p, int mode, int threads, cudaStream_t s);
+cudaError_t launch_init_spins(const KParams& p, const RunDesc* host_runs, cudaStream_t s);
+cudaError_t launch_measure(const KParams& p, int threads, cudaStream_t s);
 cudaError_t launch_resample(const KParams& p, cudaStream_t s, int64_t* launches);
 cudaError_t launch_sweep(const KParams& p, int threads, cudaStream_t s);
 cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int64_t* launches);
+cudaError_t prepare_sweep(const KParams& p, int threads);
 int sweep_threads(int N);
 bool sweep_threads_supported(int t);
 }  // namespace pa

@@ -69,8 +69,8 @@ __device__ uint64_t sys_below(uint64_t x, uint64_t R, uint64_t T, uint32_t u) {
     return n < R ? n : R;
 }
 
-__device__ __forceinline__ int level_of(int32_t E, const KParams& p) {
-    return ((E + p.d * p.N) >> 1) >> 1;  // U = (E + dN)/2, level = U >> 1
+__device__ __forceinline__ int level_of(int32_t E, int dN) {
+    return ((E + dN) >> 1) >> 1;  // U = (E + dN)/2, level = U >> 1
 }
 
 // --------------------------------------------------------------------------
@@ -110,14 +110,15 @@ __device__ __forceinline__ T block_excl_scan(T v, T* sh, T* total) {
 // K3: weights, S, ln Q, f table (one CTA)
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_weights(KParams p) {
-    DevState* st = p.st;
+    const RunDesc& r = p.runs[blockIdx.x];
+    DevState* st = r.st;
     if (st->status != S_OK) return;
     __shared__ int smin[32], smax[32];
     const int i = st->step + 1;
     const uint32_t Rprev = st->R_cur;
     int lo = INT_MAX, hi = -1;
-    for (int l = threadIdx.x; l < p.nlev; l += blockDim.x)
-        if (p.hist[l]) {
+    for (int l = threadIdx.x; l < r.nlev; l += blockDim.x)
+        if (r.hist[l]) {
             lo = min(lo, l);
             hi = max(hi, l);
         }
@@ -142,9 +143,9 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
     int P = 1;
     while (P < K) P <<= 1;
     const double q = p.q[i - 1];
-    volatile double* t = p.tree;
+    volatile double* t = r.tree;
     for (int k = threadIdx.x; k < P; k += blockDim.x)
-        t[k] = (k < K) ? __dmul_rn((double)p.hist[lmin + k], pow_bin(q, (uint32_t)k)) : 0.0;
+        t[k] = (k < K) ? __dmul_rn((double)r.hist[lmin + k], pow_bin(q, (uint32_t)k)) : 0.0;
     __threadfence_block();
     __syncthreads();
     for (int h = P >> 1; h >= 1; h >>= 1) {
@@ -153,25 +154,25 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
         __syncthreads();
     }
     const double S = t[0];
-    const double Rd = (double)p.R;
+    const double Rd = (double)r.R;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         double a = __dmul_rn(Rd, pow_bin(q, (uint32_t)k));
         a = __ddiv_rn(a, S);
         a = scalbn(a, FRAC_BITS);
-        p.flev[k] = (uint64_t)floor(a);
+        r.flev[k] = (uint64_t)floor(a);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x) p.hist[lmin + k] = 0u;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) r.hist[lmin + k] = 0u;
     if (threadIdx.x == 0) {
-        const int32_t Umin = 2 * lmin + p.parity;
-        const int32_t Emin = 2 * Umin - p.d * p.N;
+        const int32_t Umin = 2 * lmin + r.parity;
+        const int32_t Emin = 2 * Umin - p.d * r.N;
         const double lnQ = __dsub_rn(__dsub_rn(log(S), log((double)Rprev)),
                                      __dmul_rn(p.dbeta[i - 1], (double)Emin));
         st->R_prev = Rprev;
         st->lmin = (uint32_t)lmin;
         st->K = (uint32_t)K;
         st->sum_lnQ = __dadd_rn(st->sum_lnQ, lnQ);
-        TraceRow* tr = p.trace + i;
+        TraceRow* tr = r.trace + i;
         tr->lnQ = lnQ;
         tr->sum_lnQ = st->sum_lnQ;
         tr->c_ln_c = 0.0;
@@ -185,32 +186,36 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
 // --------------------------------------------------------------------------
 // per-block sums of f (and of its 2^-40 fractional part)
 // --------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t f_of(int j, const KParams& p, const int32_t* E, uint32_t lmin) {
-    return p.flev[level_of(E[j], p) - (int)lmin];
+__device__ __forceinline__ uint64_t f_of(int j, const RunDesc& r, int dN, const int32_t* E,
+                                         uint32_t lmin) {
+    return r.flev[level_of(E[j], dN) - (int)lmin];
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_fsum(KParams p) {
-    const DevState* st = p.st;
+    const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
+    const uint32_t b = blockIdx.x - r.blk0;
+    const DevState* st = r.st;
     if (st->status != S_OK) return;
     __shared__ uint64_t sh[33];
     const int i = st->step + 1;
-    const int32_t* E = p.E[(i - 1) & 1];
+    const int32_t* E = r.E[(i - 1) & 1];
     const uint32_t Rprev = st->R_prev, lmin = st->lmin;
-    const int j0 = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    const int dN = p.d * r.N;
+    const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
     uint64_t sf = 0, sg = 0;
     for (int e = 0; e < SCAN_ITEMS; ++e) {
         const int j = j0 + e;
         if ((uint32_t)j < Rprev) {
-            const uint64_t f = f_of(j, p, E, lmin);
+            const uint64_t f = f_of(j, r, dN, E, lmin);
             sf += f;
             sg += f & ((1ull << FRAC_BITS) - 1);
         }
     }
     uint64_t tot;
     block_excl_scan(sf, sh, &tot);
-    if (threadIdx.x == 0) p.partA[blockIdx.x] = tot;
+    if (threadIdx.x == 0) r.partA[b] = tot;
     block_excl_scan(sg, sh, &tot);
-    if (threadIdx.x == 0) p.partB[blockIdx.x] = tot;
+    if (threadIdx.x == 0) r.partB[b] = tot;
 }
 
 // exclusive scan of the per-block partials (one CTA of 1024 threads)
@@ -242,17 +247,18 @@ __device__ void scan_partials(const uint64_t* part, uint64_t* off, int n, uint64
 }
 
 __global__ void __launch_bounds__(1024) k_fscan(KParams p) {
-    DevState* st = p.st;
+    const RunDesc& r = p.runs[blockIdx.x];
+    DevState* st = r.st;
     if (st->status != S_OK) return;
     __shared__ uint64_t tA, tB;
-    scan_partials(p.partA, p.offA, p.nblk, &tA);
-    scan_partials(p.partB, p.offB, p.nblk, &tB);
+    scan_partials(r.partA, r.offA, r.nblk, &tA);
+    scan_partials(r.partB, r.offB, r.nblk, &tB);
     __syncthreads();
     if (threadIdx.x == 0) {
         st->T = tA;
         st->Tres = tB;
         const uint64_t A = (tA - tB) >> FRAC_BITS;  // sum of floor(f / 2^40)
-        st->Rres = (uint64_t)p.R - A;
+        st->Rres = (uint64_t)r.R - A;
     }
 }
 
@@ -260,30 +266,33 @@ __global__ void __launch_bounds__(1024) k_fscan(KParams p) {
 // prefix sums C (and G) and the copy counts of the rules that need no search
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(SCAN_THREADS) k_counts(KParams p) {
-    DevState* st = p.st;
+    const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
+    const uint32_t b = blockIdx.x - r.blk0;
+    DevState* st = r.st;
     if (st->status != S_OK) return;
     __shared__ uint64_t sh[33];
     const int i = st->step + 1;
-    const int32_t* E = p.E[(i - 1) & 1];
+    const int32_t* E = r.E[(i - 1) & 1];
+    const int dN = p.d * r.N;
     const uint32_t Rprev = st->R_prev, lmin = st->lmin;
     const uint64_t T = st->T;
-    const int j0 = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
     uint64_t f[SCAN_ITEMS];
     uint64_t sf = 0, sg = 0;
 #pragma unroll
     for (int e = 0; e < SCAN_ITEMS; ++e) {
         const int j = j0 + e;
-        f[e] = ((uint32_t)j < Rprev) ? f_of(j, p, E, lmin) : 0ull;
+        f[e] = ((uint32_t)j < Rprev) ? f_of(j, r, dN, E, lmin) : 0ull;
         sf += f[e];
         sg += f[e] & ((1ull << FRAC_BITS) - 1);
     }
     uint64_t tot;
-    uint64_t cf = block_excl_scan(sf, sh, &tot) + p.offA[blockIdx.x];
-    uint64_t cg = block_excl_scan(sg, sh, &tot) + p.offB[blockIdx.x];
+    uint64_t cf = block_excl_scan(sf, sh, &tot) + r.offA[b];
+    uint64_t cg = block_excl_scan(sg, sh, &tot) + r.offB[b];
     const int method = p.method;
     uint32_t usys = 0;
     if (method == M_SYSTEMATIC)
-        usys = philox(0u, DOM_RESAMPLE | RULE_SYSTEMATIC, (uint32_t)i, 0u, p.k0, p.k1).x;
+        usys = philox(0u, DOM_RESAMPLE | (r.run << 8) | RULE_SYSTEMATIC, (uint32_t)i, 0u, p.k0, p.k1).x;
     bool kmax = false;
 #pragma unroll 1
     for (int e = 0; e < SCAN_ITEMS; ++e) {
@@ -292,26 +301,26 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_counts(KParams p) {
         const uint64_t prevC = cf;
         cf += f[e];
         cg += f[e] & ((1ull << FRAC_BITS) - 1);
-        p.C[j] = cf;
-        if (method == M_RESIDUAL) p.G[j] = cg;
-        uint32_t r = 0;
+        r.C[j] = cf;
+        if (method == M_RESIDUAL) r.G[j] = cg;
+        uint32_t cnt = 0;
         if (method == M_NEAREST) {
-            const uint4x x = philox((uint32_t)j, DOM_RESAMPLE | RULE_NEAREST, (uint32_t)i, 0u,
+            const uint4x x = philox((uint32_t)j, DOM_RESAMPLE | (r.run << 8) | RULE_NEAREST, (uint32_t)i, 0u,
                                     p.k0, p.k1);
             const uint64_t u40 = (((uint64_t)x.y << 32) | x.x) >> 24;
-            r = (uint32_t)(f[e] >> FRAC_BITS) +
-                (u40 < (f[e] & ((1ull << FRAC_BITS) - 1)) ? 1u : 0u);
+            cnt = (uint32_t)(f[e] >> FRAC_BITS) +
+                  (u40 < (f[e] & ((1ull << FRAC_BITS) - 1)) ? 1u : 0u);
         } else if (method == M_SYSTEMATIC) {
-            r = (uint32_t)(sys_below(cf, p.R, T, usys) - sys_below(prevC, p.R, T, usys));
+            cnt = (uint32_t)(sys_below(cf, r.R, T, usys) - sys_below(prevC, r.R, T, usys));
         } else if (method == M_RESIDUAL) {
-            r = (uint32_t)(f[e] >> FRAC_BITS);
+            cnt = (uint32_t)(f[e] >> FRAC_BITS);
         } else if (method == M_POISSON) {
             const double lam = scalbn((double)f[e], -FRAC_BITS);
             const uint32_t M = (uint32_t)(f[e] >> 44) + 1u;
             const double lc = __ddiv_rn(lam, (double)M);
             uint32_t total = 0;
             for (uint32_t m = 0; m < M; ++m) {
-                const uint4x x = philox((uint32_t)j, DOM_RESAMPLE | RULE_POISSON, (uint32_t)i, m,
+                const uint4x x = philox((uint32_t)j, DOM_RESAMPLE | (r.run << 8) | RULE_POISSON, (uint32_t)i, m,
                                         p.k0, p.k1);
                 const double u = scalbn((double)((((uint64_t)x.y << 32) | x.x) >> 11), -53);
                 double pr = exp_taylor(-lc);
@@ -328,17 +337,19 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_counts(KParams p) {
                 }
                 total += k;
             }
-            r = total;
+            cnt = total;
         }
-        p.counts[j] = r;
+        r.counts[j] = cnt;
     }
     if (kmax) atomicCAS(&st->status, S_OK, S_KMAX);
 }
 
 // multinomial draws (multinomial rule: R draws over C; residual rule: R_res
 // draws over the remainders G, or over C if every remainder is zero)
-__global__ void __launch_bounds__(256) k_draws(KParams p) {
-    const DevState* st = p.st;
+__global__ void __launch_bounds__(SCAN_THREADS) k_draws(KParams p) {
+    const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
+    const uint32_t b = blockIdx.x - r.blk0;
+    const DevState* st = r.st;
     if (st->status != S_OK) return;
     const int i = st->step + 1;
     const uint32_t Rprev = st->R_prev;
@@ -347,21 +358,21 @@ __global__ void __launch_bounds__(256) k_draws(KParams p) {
     uint64_t total;
     uint32_t rule;
     if (p.method == M_MULTINOMIAL) {
-        n = p.R;
-        box = p.C;
+        n = r.R;
+        box = r.C;
         total = st->T;
         rule = RULE_MULTINOMIAL;
     } else {
         n = st->Rres;
         const bool use_g = st->Tres > 0;
-        box = use_g ? p.G : p.C;
+        box = use_g ? r.G : r.C;
         total = use_g ? st->Tres : st->T;
         rule = RULE_RESIDUAL;
     }
-    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4x x = philox((uint32_t)(k >> 1), DOM_RESAMPLE | rule, (uint32_t)i, 0u, p.k0,
-                                p.k1);
+    const uint64_t stride = (uint64_t)r.nblk * SCAN_THREADS;
+    for (uint64_t k = (uint64_t)b * SCAN_THREADS + threadIdx.x; k < n; k += stride) {
+        const uint4x x = philox((uint32_t)(k >> 1), DOM_RESAMPLE | (r.run << 8) | rule, (uint32_t)i,
+                                0u, p.k0, p.k1);
         const uint64_t u = (k & 1) ? (((uint64_t)x.w << 32) | x.z) : (((uint64_t)x.y << 32) | x.x);
         const uint64_t pos = __umul64hi(u, total);
         uint32_t lo = 0, hi = Rprev;
@@ -370,7 +381,7 @@ __global__ void __launch_bounds__(256) k_draws(KParams p) {
             if (pos < box[mid]) hi = mid;
             else lo = mid + 1;
         }
-        atomicAdd(&p.counts[lo], 1u);
+        atomicAdd(&r.counts[lo], 1u);
     }
 }
 
@@ -378,61 +389,67 @@ __global__ void __launch_bounds__(256) k_draws(KParams p) {
 // scan of the counts and scatter of the ancestor array
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(SCAN_THREADS) k_rsum(KParams p) {
-    const DevState* st = p.st;
+    const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
+    const uint32_t b = blockIdx.x - r.blk0;
+    const DevState* st = r.st;
     if (st->status != S_OK) return;
     __shared__ uint64_t sh[33];
     const uint32_t Rprev = st->R_prev;
-    const int j0 = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
     uint64_t s = 0;
     for (int e = 0; e < SCAN_ITEMS; ++e) {
         const int j = j0 + e;
-        if ((uint32_t)j < Rprev) s += p.counts[j];
+        if ((uint32_t)j < Rprev) s += r.counts[j];
     }
     uint64_t tot;
     block_excl_scan(s, sh, &tot);
-    if (threadIdx.x == 0) p.partA[blockIdx.x] = tot;
+    if (threadIdx.x == 0) r.partA[b] = tot;
 }
 
 __global__ void __launch_bounds__(1024) k_rscan(KParams p) {
-    DevState* st = p.st;
+    const RunDesc& r = p.runs[blockIdx.x];
+    DevState* st = r.st;
     if (st->status != S_OK) return;
     __shared__ uint64_t tA;
-    scan_partials(p.partA, p.offA, p.nblk, &tA);
+    scan_partials(r.partA, r.offA, r.nblk, &tA);
     __syncthreads();
     if (threadIdx.x == 0) {
         // a population that outgrows its capacity, or dies out, stops the run
-        if (tA > (uint64_t)p.Rcap || tA == 0) st->status = S_CAPACITY;
+        if (tA > (uint64_t)r.Rcap || tA == 0) st->status = S_CAPACITY;
         else st->R_cur = (uint32_t)tA;
     }
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scatter(KParams p) {
-    const DevState* st = p.st;
+    const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
+    const uint32_t b = blockIdx.x - r.blk0;
+    const DevState* st = r.st;
     if (st->status != S_OK) return;
     __shared__ uint64_t sh[33];
     __shared__ double sd[SCAN_THREADS];
     const int i = st->step + 1;
-    const int32_t* E = p.E[(i - 1) & 1];
+    const int32_t* E = r.E[(i - 1) & 1];
+    const int dN = p.d * r.N;
     const uint32_t Rprev = st->R_prev, lmin = st->lmin;
-    const int j0 = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
-    uint32_t r[SCAN_ITEMS];
+    const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    uint32_t rc[SCAN_ITEMS];
     uint64_t s = 0;
 #pragma unroll
     for (int e = 0; e < SCAN_ITEMS; ++e) {
         const int j = j0 + e;
-        r[e] = ((uint32_t)j < Rprev) ? p.counts[j] : 0u;
-        s += r[e];
+        rc[e] = ((uint32_t)j < Rprev) ? r.counts[j] : 0u;
+        s += rc[e];
     }
     uint64_t tot;
-    uint64_t o = block_excl_scan(s, sh, &tot) + p.offA[blockIdx.x];
+    uint64_t o = block_excl_scan(s, sh, &tot) + r.offA[b];
     double sv = 0.0;
     for (int e = 0; e < SCAN_ITEMS; ++e) {
         const int j = j0 + e;
         if ((uint32_t)j >= Rprev) break;
-        for (uint32_t c = 0; c < r[e]; ++c) p.anc[o + c] = (uint32_t)j;
-        o += r[e];
-        const double tau = scalbn((double)f_of(j, p, E, lmin), -FRAC_BITS);
-        const double dl = __dsub_rn((double)r[e], tau);
+        for (uint32_t c = 0; c < rc[e]; ++c) r.anc[o + c] = (uint32_t)j;
+        o += rc[e];
+        const double tau = scalbn((double)f_of(j, r, dN, E, lmin), -FRAC_BITS);
+        const double dl = __dsub_rn((double)rc[e], tau);
         sv = __dadd_rn(sv, __dmul_rn(dl, dl));
     }
     // fixed-order tree reduction of the block's sampling-variance terms
@@ -442,23 +459,25 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scatter(KParams p) {
         if ((int)threadIdx.x < h) sd[threadIdx.x] = __dadd_rn(sd[threadIdx.x], sd[threadIdx.x + h]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) p.partD[blockIdx.x] = sd[0];
+    if (threadIdx.x == 0) r.partD[b] = sd[0];
 }
 
 // --------------------------------------------------------------------------
 // family statistics of the new population (families stay sorted by slot)
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
-    const DevState* st = p.st;
+    const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
+    const uint32_t b = blockIdx.x - r.blk0;
+    const DevState* st = r.st;
     if (st->status != S_OK) return;
     __shared__ double sd[SCAN_THREADS];
     __shared__ unsigned long long sc2;
     const int i = (mode == 0) ? st->step + 1 : st->step;
     const uint32_t Ri = st->R_cur;
-    const uint32_t* fam = p.fam[i & 1];
+    const uint32_t* fam = r.fam[i & 1];
     if (threadIdx.x == 0) sc2 = 0ull;
     __syncthreads();
-    const int j0 = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
     double cl = 0.0;
     unsigned long long c2 = 0;
     for (int e = 0; e < SCAN_ITEMS; ++e) {
@@ -485,22 +504,23 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        p.partCL[blockIdx.x] = sd[0];
-        if (sc2) atomicAdd(&p.trace[i].sumC2, sc2);
+        r.partCL[b] = sd[0];
+        if (sc2) atomicAdd(&r.trace[i].sumC2, sc2);
     }
 }
 
 // fixed-order sums of the per-block partials, close the step
 __global__ void __launch_bounds__(256) k_finish(KParams p, int mode) {
-    DevState* st = p.st;
+    const RunDesc& r = p.runs[blockIdx.x];
+    DevState* st = r.st;
     if (st->status != S_OK) return;
     __shared__ double a[256], b[256];
     const int i = (mode == 0) ? st->step + 1 : st->step;
     const int nb_sv = (mode == 0) ? (int)((st->R_prev + SCAN_CHUNK - 1) / SCAN_CHUNK) : 0;
     const int nb_f = (int)((st->R_cur + SCAN_CHUNK - 1) / SCAN_CHUNK);
     double sa = 0.0, sb = 0.0;
-    for (int k = threadIdx.x; k < nb_sv; k += blockDim.x) sa = __dadd_rn(sa, p.partD[k]);
-    for (int k = threadIdx.x; k < nb_f; k += blockDim.x) sb = __dadd_rn(sb, p.partCL[k]);
+    for (int k = threadIdx.x; k < nb_sv; k += blockDim.x) sa = __dadd_rn(sa, r.partD[k]);
+    for (int k = threadIdx.x; k < nb_f; k += blockDim.x) sb = __dadd_rn(sb, r.partCL[k]);
     a[threadIdx.x] = sa;
     b[threadIdx.x] = sb;
     __syncthreads();
@@ -512,7 +532,7 @@ __global__ void __launch_bounds__(256) k_finish(KParams p, int mode) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        TraceRow* tr = p.trace + i;
+        TraceRow* tr = r.trace + i;
         tr->sv_sum = a[0];
         tr->c_ln_c = b[0];
         tr->R_i = st->R_cur;
@@ -523,29 +543,26 @@ __global__ void __launch_bounds__(256) k_finish(KParams p, int mode) {
 
 // --------------------------------------------------------------------------
 cudaError_t launch_resample(const KParams& p, cudaStream_t s, int64_t* launches) {
-    k_weights<<<1, 1024, 0, s>>>(p);
-    k_fsum<<<p.nblk, SCAN_THREADS, 0, s>>>(p);
-    k_fscan<<<1, 1024, 0, s>>>(p);
-    k_counts<<<p.nblk, SCAN_THREADS, 0, s>>>(p);
+    k_weights<<<p.M, 1024, 0, s>>>(p);
+    k_fsum<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
+    k_fscan<<<p.M, 1024, 0, s>>>(p);
+    k_counts<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
     int n = 4;
     if (p.method == M_MULTINOMIAL || p.method == M_RESIDUAL) {
-        int grid = (int)((p.R + 255u) / 256u);
-        if (grid > 4096) grid = 4096;
-        k_draws<<<grid, 256, 0, s>>>(p);
+        k_draws<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
         ++n;
     }
-    k_rsum<<<p.nblk, SCAN_THREADS, 0, s>>>(p);
-    k_rscan<<<1, 1024, 0, s>>>(p);
-    k_scatter<<<p.nblk, SCAN_THREADS, 0, s>>>(p);
+    k_rsum<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
+    k_rscan<<<p.M, 1024, 0, s>>>(p);
+    k_scatter<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
     n += 3;
     if (launches) *launches += n;
     return cudaGetLastError();
 }
 
 cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int64_t* launches) {
-    int nb = (int)((p.Rcap + SCAN_CHUNK - 1) / SCAN_CHUNK);
-    k_family<<<nb, SCAN_THREADS, 0, s>>>(p, mode);
-    k_finish<<<1, 256, 0, s>>>(p, mode);
+    k_family<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p, mode);
+    k_finish<<<p.M, 256, 0, s>>>(p, mode);
     if (launches) *launches += 2;
     return cudaGetLastError();
 }

@@ -39,8 +39,14 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
     return x;
 }
 
-__device__ __forceinline__ int div_L(int s, const KParams& p) {
-    return (int)(((uint64_t)(uint32_t)s * p.magicL) >> p.shiftL);
+// lattice geometry of the CTA's run
+struct Geo {
+    int L, N;
+    uint32_t magicL, shiftL;
+};
+
+__device__ __forceinline__ int div_L(int s, const Geo& g) {
+    return (int)(((uint64_t)(uint32_t)s * g.magicL) >> g.shiftL);
 }
 
 // ---------------------------------------------------------------------------
@@ -48,24 +54,25 @@ __device__ __forceinline__ int div_L(int s, const KParams& p) {
 // Thread (j, g) writes words 4g..4g+3 of replica j from one INIT draw.
 // ---------------------------------------------------------------------------
 __global__ void k_init_spins(KParams p) {
-    const uint32_t nq = (uint32_t)(p.Wp >> 2);
+    const RunDesc& r = p.runs[blockIdx.y];
+    const uint32_t nq = (uint32_t)(r.Wp >> 2);
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t total = (uint64_t)p.R * nq;
+    const uint64_t total = (uint64_t)r.R * nq;
     if (tid >= total) return;
     const uint32_t j = (uint32_t)(tid / nq);
     const uint32_t g = (uint32_t)(tid - (uint64_t)j * nq);
-    uint4x x = philox(g, DOM_INIT, 0u, j, p.k0, p.k1);
+    uint4x x = philox(g, DOM_INIT, 0u, 32u * r.grp0 + j, p.k0, p.k1);
     uint32_t w[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int word = 4 * (int)g + m;
         const int lo = 32 * word;
-        if (lo >= p.N) w[m] = 0u;
-        else if (p.N - lo < 32) w[m] &= (1u << (p.N - lo)) - 1u;
+        if (lo >= r.N) w[m] = 0u;
+        else if (r.N - lo < 32) w[m] &= (1u << (r.N - lo)) - 1u;
     }
-    uint4* dst = reinterpret_cast<uint4*>(p.spins[0] + (size_t)j * p.Wp) + g;
+    uint4* dst = reinterpret_cast<uint4*>(r.spins[0] + (size_t)j * r.Wp) + g;
     *dst = make_uint4(w[0], w[1], w[2], w[3]);
-    if (g == 0) p.fam[0][j] = j;
+    if (g == 0) r.fam[0][j] = j;
 }
 
 // ---------------------------------------------------------------------------
@@ -126,15 +133,15 @@ struct SiteCmp {
 
 template <int D, bool EA>
 __device__ __forceinline__ void site_prepare(SiteCmp<D>& c, const uint32_t* ms, const uint8_t* jb,
-                                             const KParams& p, int k, int colour, uint32_t A2x,
+                                             const Geo& geo, int k, int colour, uint32_t A2x,
                                              uint32_t B1k, uint32_t vmask) {
-    const int L = p.L;
+    const int L = geo.L;
     const int LL = L * L;
     const int s0 = 2 * k;
-    int q1 = div_L(s0, p);
+    int q1 = div_L(s0, geo);
     int x = s0 - q1 * L, y, z = 0;
     if (D == 3) {
-        z = div_L(q1, p);
+        z = div_L(q1, geo);
         y = q1 - z * L;
     } else {
         y = q1;
@@ -320,28 +327,32 @@ __host__ __device__ __forceinline__ int queue_capacity(int N) {
 template <int D, bool EA, int NT>
 __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
     extern __shared__ __align__(16) uint32_t smem[];
+    // the CTA's run and its replica group within the run; the flattened CTA
+    // index is the global replica group of the sweep draws
+    const RunDesc& r = p.runs[p.grp2run[blockIdx.x]];
+    const Geo geo = {r.L, r.N, r.magicL, r.shiftL};
     uint32_t* ms = smem;
-    uint8_t* jb = reinterpret_cast<uint8_t*>(smem + p.N);
-    const int qcap = queue_capacity(p.N);
-    uint32_t* qwords = smem + p.N + (p.ea ? (p.N + 15) / 16 * 4 : 0);
+    uint8_t* jb = reinterpret_cast<uint8_t*>(smem + r.N);
+    const int qcap = queue_capacity(r.N);
+    uint32_t* qwords = smem + r.N + (EA ? (r.N + 15) / 16 * 4 : 0);
     __shared__ int32_t sU[32];
     __shared__ int32_t sNup[32];
     __shared__ unsigned long long sAcc;
     __shared__ PlaneTab tabs[2][8];
     __shared__ int qn[2];
 
-    const DevState* st = p.st;
+    const DevState* st = r.st;
     if (st->status != S_OK) return;
     const int i = (mode == 0) ? st->step + 1 : st->step;
     const uint32_t R = st->R_cur;
-    const uint32_t base = blockIdx.x * 32u;
+    const uint32_t base = (blockIdx.x - r.grp0) * 32u;
     if (base >= R) return;
     const uint32_t nval = min(32u, R - base);
     const uint32_t vmask = (nval == 32u) ? 0xFFFFFFFFu : ((1u << nval) - 1u);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int N = p.N, W = p.W, Wp = p.Wp;
-    const uint32_t* src = p.spins[mode == 0 ? ((i - 1) & 1) : (i & 1)];
-    uint32_t* dst = p.spins[i & 1];
+    const int N = r.N, W = r.W, Wp = r.Wp;
+    const uint32_t* src = r.spins[mode == 0 ? ((i - 1) & 1) : (i & 1)];
+    uint32_t* dst = r.spins[i & 1];
 
     if (threadIdx.x < 32) {
         sU[threadIdx.x] = 0;
@@ -351,8 +362,8 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
 
     const bool valid = (uint32_t)lane < nval;
     uint32_t my_src = base + lane;
-    if (mode == 0 && valid) my_src = p.anc[base + lane];
-    if (mode == 0 && warp == 0 && valid) p.fam[i & 1][base + lane] = p.fam[(i - 1) & 1][my_src];
+    if (mode == 0 && valid) my_src = r.anc[base + lane];
+    if (mode == 0 && warp == 0 && valid) r.fam[i & 1][base + lane] = r.fam[(i - 1) & 1][my_src];
 
     // gather the 32 parent rows and transpose them into the multi-spin layout
     for (int c4 = warp; 4 * c4 < W; c4 += nwarp) {
@@ -370,7 +381,7 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
         }
     }
     if (EA)
-        for (int s = threadIdx.x; s < N; s += blockDim.x) jb[s] = p.jbits[s];
+        for (int s = threadIdx.x; s < N; s += blockDim.x) jb[s] = r.jbits[s];
     __syncthreads();
 
     uint32_t acc = 0;
@@ -379,7 +390,7 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
         uint32_t thr[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) thr[k] = p.thr[4 * (i - 1) + k];
-        const uint32_t grp = base >> 5;
+        const uint32_t grp = blockIdx.x;         // global replica group
         uint32_t h0a, l0a, h1a, l1a;
         mulhilo(PHILOX_M0, grp, h0a, l0a);
         mulhilo(PHILOX_M1, (uint32_t)i, h1a, l1a);
@@ -408,7 +419,7 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
             // pass 1: every site runs plane blocks 0 and 1 (decides ~88% of sites)
             for (int k = threadIdx.x; k < nhalf; k += blockDim.x) {
                 SiteCmp<D> c;
-                site_prepare<D, EA>(c, ms, jb, p, k, colour, A2x, B1k, vmask);
+                site_prepare<D, EA>(c, ms, jb, geo, k, colour, A2x, B1k, vmask);
                 if (c.need) {
                     uint32_t W[4], V[4];
                     block_draw2<D>(c, tab[0], tab[1], p, W, V);
@@ -460,15 +471,15 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
                 // unsatisfied-bond planes of the + bonds of s (0 past the last site)
                 uint32_t P0 = 0u, P1 = 0u, P2 = 0u;
                 if (in) {
-                    int q1 = div_L(s, p);
-                    int x = s - q1 * p.L, y, z = 0;
+                    int q1 = div_L(s, geo);
+                    int x = s - q1 * geo.L, y, z = 0;
                     if (D == 3) {
-                        z = div_L(q1, p);
-                        y = q1 - z * p.L;
+                        z = div_L(q1, geo);
+                        y = q1 - z * geo.L;
                     } else {
                         y = q1;
                     }
-                    const int L = p.L;
+                    const int L = geo.L;
                     const int xp = (x == L - 1) ? s - (L - 1) : s + 1;
                     const int yp = (y == L - 1) ? s - (L - 1) * L : s + L;
                     const uint32_t js = EA ? (uint32_t)jb[s] : 0u;
@@ -500,11 +511,11 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
         long long e = 0, e2 = 0, am = 0, m2 = 0;
         if (valid) {
             const int32_t Uv = sU[lane];
-            const int32_t E = 2 * Uv - p.d * N;
+            const int32_t E = 2 * Uv - D * N;
             const int32_t M = N - 2 * sNup[lane];
-            p.E[i & 1][base + lane] = E;
-            p.M[base + lane] = M;
-            atomicAdd(&p.hist[Uv >> 1], 1u);
+            r.E[i & 1][base + lane] = E;
+            r.M[base + lane] = M;
+            atomicAdd(&r.hist[Uv >> 1], 1u);
             e = E;
             e2 = (long long)E * E;
             am = M < 0 ? -M : M;
@@ -517,7 +528,7 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
             m2 += __shfl_xor_sync(0xffffffffu, m2, o);
         }
         if (lane == 0) {
-            TraceRow* tr = p.trace + i;
+            TraceRow* tr = r.trace + i;
             atomicAdd(&tr->sumE, (unsigned long long)e);
             atomicAdd(&tr->sumE2, (unsigned long long)e2);
             atomicAdd(&tr->sumAbsM, (unsigned long long)am);
@@ -538,13 +549,12 @@ bool sweep_threads_supported(int t) { return t == 64 || t == 128 || t == 256 || 
 
 static size_t group_smem(const KParams& p) {
     const size_t words_per_entry = 7 + (size_t)p.d;
-    return (size_t)p.N * 4 + (p.ea ? (size_t)((p.N + 15) / 16) * 16 : 0) +
-           words_per_entry * 4 * (size_t)queue_capacity(p.N);
+    return (size_t)p.maxN * 4 + (p.ea ? (size_t)((p.maxN + 15) / 16) * 16 : 0) +
+           words_per_entry * 4 * (size_t)queue_capacity(p.maxN);
 }
 
 template <int D, bool EA, int NT>
-static cudaError_t launch_group_nt(const KParams& p, int mode, cudaStream_t s) {
-    const size_t smem = group_smem(p);
+static cudaError_t prepare_nt() {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_group<D, EA, NT>,
@@ -553,8 +563,14 @@ static cudaError_t launch_group_nt(const KParams& p, int mode, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const unsigned grid = (p.Rcap + 31u) / 32u;
-    k_group<D, EA, NT><<<grid, NT, smem, s>>>(p, mode);
+    return cudaSuccess;
+}
+
+template <int D, bool EA, int NT>
+static cudaError_t launch_group_nt(const KParams& p, int mode, cudaStream_t s) {
+    cudaError_t e = prepare_nt<D, EA, NT>();
+    if (e != cudaSuccess) return e;
+    k_group<D, EA, NT><<<p.ngrp_total, NT, group_smem(p), s>>>(p, mode);
     return cudaGetLastError();
 }
 
@@ -575,15 +591,35 @@ static cudaError_t launch_group(const KParams& p, int mode, int threads, cudaStr
                 : launch_group_t<3, false>(p, mode, threads, s);
 }
 
-cudaError_t launch_init_spins(const KParams& p, cudaStream_t s) {
-    const uint64_t total = (uint64_t)p.R * (uint64_t)(p.Wp / 4);
-    const unsigned grid = (unsigned)((total + 255) / 256);
+template <int D, bool EA>
+static cudaError_t prepare_t(int threads) {
+    switch (threads) {
+        case 64: return prepare_nt<D, EA, 64>();
+        case 128: return prepare_nt<D, EA, 128>();
+        case 512: return prepare_nt<D, EA, 512>();
+        default: return prepare_nt<D, EA, 256>();
+    }
+}
+
+// one-time function attributes, outside any stream capture
+cudaError_t prepare_sweep(const KParams& p, int threads) {
+    if (p.d == 2) return p.ea ? prepare_t<2, true>(threads) : prepare_t<2, false>(threads);
+    return p.ea ? prepare_t<3, true>(threads) : prepare_t<3, false>(threads);
+}
+
+cudaError_t launch_init_spins(const KParams& p, const RunDesc* host_runs, cudaStream_t s) {
+    uint64_t most = 0;
+    for (int m = 0; m < p.M; ++m) {
+        const uint64_t t = (uint64_t)host_runs[m].R * (uint64_t)(host_runs[m].Wp / 4);
+        if (t > most) most = t;
+    }
+    const dim3 grid((unsigned)((most + 255) / 256), (unsigned)p.M);
     k_init_spins<<<grid, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_measure(const KParams& p, int mode, int threads, cudaStream_t s) {
-    return launch_group(p, mode, threads, s);
+cudaError_t launch_measure(const KParams& p, int threads, cudaStream_t s) {
+    return launch_group(p, 1, threads, s);
 }
 
 cudaError_t launch_sweep(const KParams& p, int threads, cudaStream_t s) {

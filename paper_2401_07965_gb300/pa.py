@@ -30,7 +30,10 @@ PA_ARRAY_COUNTS, PA_ARRAY_ANCESTOR, PA_ARRAY_MAGNET = 3, 4, 5
 EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observables", "pa_trace",
            "pa_free_energy", "pa_get_array", "pa_set_state", "pa_enable_timing",
            "pa_sweep_timing", "pa_launch_count", "pa_destroy", "pa_strerror",
-           "pa_weights_static", "pa_set_sweep_threads", "pa_get_sweep_threads"]
+           "pa_weights_static", "pa_set_sweep_threads", "pa_get_sweep_threads",
+           "pa_batch_workspace_bytes", "pa_batch_init", "pa_batch_size", "pa_run_observables",
+           "pa_run_trace", "pa_run_free_energy", "pa_run_get_array", "pa_weighted",
+           "pa_set_graph"]
 
 
 class pa_lattice(C.Structure):
@@ -59,6 +62,23 @@ class pa_obs(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad0"}
+
+
+class pa_run_spec(C.Structure):
+    _fields_ = [("lattice", pa_lattice), ("couplings", pa_couplings), ("R", C.c_uint32),
+                ("R_cap", C.c_uint32), ("ensemble", C.c_int32)]
+
+
+class pa_weighted_obs(C.Structure):
+    _fields_ = [("step", C.c_int32), ("n_runs", C.c_int32), ("beta", C.c_double),
+                ("lnZ", C.c_double), ("minus_beta_F", C.c_double), ("w_max", C.c_double),
+                ("eff_runs", C.c_double), ("e", C.c_double), ("e2", C.c_double),
+                ("absm", C.c_double), ("m2", C.c_double), ("c", C.c_double), ("chi", C.c_double),
+                ("c_naive", C.c_double), ("chi_naive", C.c_double), ("e_plain", C.c_double),
+                ("c_plain", C.c_double), ("chi_plain", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PAError(RuntimeError):
@@ -95,6 +115,22 @@ def _load():
     lib.pa_destroy.argtypes = [vp]
     lib.pa_weights_static.argtypes = [vp, C.c_uint32, C.c_uint32, C.c_int32, C.c_int32,
                                       C.c_int32, C.c_double, vp, vp, vp]
+    lib.pa_batch_workspace_bytes.argtypes = [C.POINTER(pa_run_spec), C.c_int32, C.c_int32,
+                                             C.c_int]
+    lib.pa_batch_workspace_bytes.restype = sz
+    lib.pa_batch_init.argtypes = [C.POINTER(vp), C.POINTER(pa_run_spec), C.c_int32,
+                                  C.POINTER(pa_schedule), C.c_int, C.c_uint64, vp, vp, sz]
+    lib.pa_batch_size.argtypes = [vp]
+    lib.pa_batch_size.restype = C.c_int32
+    lib.pa_run_observables.argtypes = [vp, C.c_int32, C.POINTER(pa_obs)]
+    lib.pa_run_trace.argtypes = [vp, C.c_int32, C.POINTER(pa_obs), C.c_int32,
+                                 C.POINTER(C.c_int32)]
+    lib.pa_run_free_energy.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]
+    lib.pa_run_get_array.argtypes = [vp, C.c_int32, C.c_int, vp, sz, C.POINTER(sz)]
+    lib.pa_weighted.argtypes = [vp, C.c_int32, C.POINTER(pa_weighted_obs), C.c_int32,
+                                C.POINTER(C.c_int32)]
+    lib.pa_set_graph.argtypes = [vp, C.c_int32]
     lib.pa_set_sweep_threads.argtypes = [vp, C.c_int32]
     lib.pa_get_sweep_threads.argtypes = [vp]
     lib.pa_get_sweep_threads.restype = C.c_int32
@@ -102,7 +138,7 @@ def _load():
     lib.pa_strerror.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("pa_workspace_bytes", "pa_launch_count", "pa_strerror",
-                        "pa_get_sweep_threads"):
+                        "pa_get_sweep_threads", "pa_batch_workspace_bytes", "pa_batch_size"):
             getattr(lib, name).restype = C.c_int
     return lib
 
@@ -117,6 +153,37 @@ def _check(status, where):
 
 def _lat(dim, L):
     return pa_lattice(int(dim), int(L))
+
+
+def _couplings(couplings, keep):
+    """('ferro',), ('ea', disorder_seed, realization) or ('explicit', J int8 array)."""
+    if couplings[0] == "ferro":
+        return pa_couplings(PA_COUPLING_FERRO, 0, 0, None)
+    if couplings[0] == "ea":
+        return pa_couplings(PA_COUPLING_EA_PM, int(couplings[2]), int(couplings[1]), None)
+    if couplings[0] == "explicit":
+        J = np.ascontiguousarray(couplings[1], np.int8)
+        keep.append(J)
+        return pa_couplings(PA_COUPLING_EXPLICIT, 0, 0, J.ctypes.data_as(C.POINTER(C.c_int8)))
+    raise ValueError(f"unknown couplings {couplings[0]!r}")
+
+
+def _schedule(betas, thetas, keep):
+    b = np.ascontiguousarray(betas, np.float64)
+    t = np.ascontiguousarray(thetas, np.uint32)
+    keep += [b, t]
+    return pa_schedule(len(b) - 1, b.ctypes.data_as(C.POINTER(C.c_double)),
+                       t.ctypes.data_as(C.POINTER(C.c_uint32)))
+
+
+def _specs(runs, keep):
+    """runs: list of dicts with dim, L, R, optional R_cap, couplings, ensemble."""
+    arr = (pa_run_spec * len(runs))()
+    for k, r in enumerate(runs):
+        arr[k] = pa_run_spec(_lat(r["dim"], r["L"]), _couplings(r.get("couplings", ("ferro",)),
+                                                               keep),
+                             int(r["R"]), int(r.get("R_cap", 0)), int(r.get("ensemble", 0)))
+    return arr
 
 
 # ---- the C entry points, one to one ---------------------------------------------------------
@@ -135,24 +202,13 @@ def pa_init(dim, L, couplings, R, R_cap, betas, thetas, resampler, seed, stream=
     """couplings: ('ferro',), ('ea', disorder_seed, realization) or ('explicit', J int8 array)."""
     lat = _lat(dim, L)
     keep = []
-    if couplings[0] == "ferro":
-        cpl = pa_couplings(PA_COUPLING_FERRO, 0, 0, None)
-    elif couplings[0] == "ea":
-        cpl = pa_couplings(PA_COUPLING_EA_PM, int(couplings[2]), int(couplings[1]), None)
-    elif couplings[0] == "explicit":
-        J = np.ascontiguousarray(couplings[1], np.int8)
-        keep.append(J)
-        cpl = pa_couplings(PA_COUPLING_EXPLICIT, 0, 0, J.ctypes.data_as(C.POINTER(C.c_int8)))
-    else:
-        raise ValueError(f"unknown couplings {couplings[0]!r}")
-    b = np.ascontiguousarray(betas, np.float64)
-    t = np.ascontiguousarray(thetas, np.uint32)
-    sch = pa_schedule(len(b) - 1, b.ctypes.data_as(C.POINTER(C.c_double)),
-                      t.ctypes.data_as(C.POINTER(C.c_uint32)))
+    cpl = _couplings(couplings, keep)
+    sch = _schedule(betas, thetas, keep)
     ctx = C.c_void_p()
     st = _lib.pa_init(C.byref(ctx), C.byref(lat), C.byref(cpl), int(R), int(R_cap), C.byref(sch),
                       int(resampler), int(seed) & (2 ** 64 - 1), C.c_void_p(stream),
                       C.c_void_p(workspace), int(workspace_bytes))
+    del keep
     _check(st, "pa_init")
     return ctx
 
@@ -234,6 +290,66 @@ def pa_set_sweep_threads(ctx, threads):
 
 def pa_get_sweep_threads(ctx) -> int:
     return int(_lib.pa_get_sweep_threads(ctx))
+
+
+def pa_batch_workspace_bytes(runs, n_steps, resampler) -> int:
+    keep = []
+    specs = _specs(runs, keep)
+    return int(_lib.pa_batch_workspace_bytes(specs, len(runs), n_steps, int(resampler)))
+
+
+def pa_batch_init(runs, betas, thetas, resampler, seed, stream=0, workspace=0,
+                  workspace_bytes=0):
+    keep = []
+    specs = _specs(runs, keep)
+    sch = _schedule(betas, thetas, keep)
+    ctx = C.c_void_p()
+    _check(_lib.pa_batch_init(C.byref(ctx), specs, len(runs), C.byref(sch), int(resampler),
+                              int(seed) & (2 ** 64 - 1), C.c_void_p(stream),
+                              C.c_void_p(workspace), int(workspace_bytes)), "pa_batch_init")
+    return ctx
+
+
+def pa_batch_size(ctx) -> int:
+    return int(_lib.pa_batch_size(ctx))
+
+
+def pa_run_observables(ctx, run) -> dict:
+    o = pa_obs()
+    _check(_lib.pa_run_observables(ctx, int(run), C.byref(o)), "pa_run_observables")
+    return o.as_dict()
+
+
+def pa_run_trace(ctx, run, max_rows) -> list:
+    rows = (pa_obs * max_rows)()
+    n = C.c_int32()
+    _check(_lib.pa_run_trace(ctx, int(run), rows, max_rows, C.byref(n)), "pa_run_trace")
+    return [rows[i].as_dict() for i in range(n.value)]
+
+
+def pa_run_free_energy(ctx, run):
+    a, b = C.c_double(), C.c_double()
+    _check(_lib.pa_run_free_energy(ctx, int(run), C.byref(a), C.byref(b)), "pa_run_free_energy")
+    return a.value, b.value
+
+
+def pa_run_get_array(ctx, run, which, capacity):
+    out = np.zeros(int(capacity), _ARRAY_DTYPE[which])
+    n = C.c_size_t()
+    _check(_lib.pa_run_get_array(ctx, int(run), int(which), out.ctypes.data_as(C.c_void_p),
+                                 out.size, C.byref(n)), "pa_run_get_array")
+    return out[: n.value]
+
+
+def pa_weighted(ctx, ensemble, max_rows) -> list:
+    rows = (pa_weighted_obs * max_rows)()
+    n = C.c_int32()
+    _check(_lib.pa_weighted(ctx, int(ensemble), rows, max_rows, C.byref(n)), "pa_weighted")
+    return [rows[i].as_dict() for i in range(n.value)]
+
+
+def pa_set_graph(ctx, on=True):
+    _check(_lib.pa_set_graph(ctx, 1 if on else 0), "pa_set_graph")
 
 
 def pa_destroy(ctx):
@@ -336,3 +452,85 @@ def default_capacity(R, resampler):
     if resampler in (PA_POISSON, PA_NEAREST, "poisson", "nearest"):
         return R + int(math.ceil(10 * math.sqrt(R))) + 64
     return R
+
+
+class Batch:
+    """Several PA runs advanced together (one launch per phase for all runs).
+
+    runs: list of dicts {dim, L, R, R_cap?, couplings?, ensemble?}; all runs share the
+    dimension, coupling kind, rule, schedule and seed; run m's draws carry its identity."""
+
+    def __init__(self, runs, betas, thetas, resampler="systematic", seed=1, stream=None,
+                 use_torch_memory=True, sweep_threads=None, graph=True):
+        self.specs = [dict(r) for r in runs]
+        self.M = len(runs)
+        self.betas = np.ascontiguousarray(betas, np.float64)
+        self.thetas = np.ascontiguousarray(thetas, np.uint32)
+        self.n_steps = len(self.betas) - 1
+        self.resampler = RESAMPLERS[resampler] if isinstance(resampler, str) else int(resampler)
+        self._ws = None
+        ws_ptr, ws_bytes, stream_ptr = 0, 0, 0
+        if use_torch_memory:
+            import torch
+            nbytes = pa_batch_workspace_bytes(self.specs, self.n_steps, self.resampler)
+            if nbytes == 0:
+                raise PAError(PA_ERR_ARG, "pa_batch_workspace_bytes")
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            ws_ptr = (self._ws.data_ptr() + 255) & ~255
+            ws_bytes = nbytes
+            s = stream if stream is not None else torch.cuda.current_stream()
+            stream_ptr = s.cuda_stream
+        elif stream is not None:
+            stream_ptr = stream.cuda_stream
+        self.ctx = pa_batch_init(self.specs, self.betas, self.thetas, self.resampler, seed,
+                                 stream_ptr, ws_ptr, ws_bytes)
+        if sweep_threads:
+            pa_set_sweep_threads(self.ctx, sweep_threads)
+        pa_set_graph(self.ctx, graph)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            pa_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        pa_step(self.ctx, n)
+
+    def observables(self, run):
+        return pa_run_observables(self.ctx, run)
+
+    def trace(self, run):
+        return pa_run_trace(self.ctx, run, self.n_steps + 1)
+
+    def free_energy(self, run):
+        return pa_run_free_energy(self.ctx, run)
+
+    def weighted(self, ensemble):
+        return pa_weighted(self.ctx, ensemble, self.n_steps + 1)
+
+    def array(self, run, which):
+        spec = self.specs[run]
+        cap = spec.get("R_cap") or default_capacity(spec["R"], self.resampler)
+        if which == PA_ARRAY_SPINS:
+            cap *= (spec["L"] ** spec["dim"] + 31) // 32
+        return pa_run_get_array(self.ctx, run, which, cap)
+
+    def spins_words(self, run):
+        spec = self.specs[run]
+        W = (spec["L"] ** spec["dim"] + 31) // 32
+        return self.array(run, PA_ARRAY_SPINS).reshape(-1, W)
+
+    def slot_bases(self):
+        """32 x the sweep CTAs of the preceding runs: the replica-slot offset of each run."""
+        out, acc = [], 0
+        for spec in self.specs:
+            out.append(acc)
+            cap = spec.get("R_cap") or default_capacity(spec["R"], self.resampler)
+            acc += 32 * ((cap + 31) // 32)
+        return out
