@@ -366,6 +366,130 @@ def run_small(args):
     return 0
 
 
+def _kaufman(L, beta):
+    with open(os.path.join(ROOT, "tests", "golden", "kaufman_lnZ.txt")) as fh:
+        for ln in fh:
+            if ln.startswith("#"):
+                continue
+            l, b, v = ln.split()
+            if int(l) == L and abs(float(b) - beta) < 1e-12:
+                return float(v)
+    return None
+
+
+def _timed_batch(pa, batch, n_steps, stream):
+    """Device time of n_steps graph-replayed temperature steps of a batch (CUDA events)."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    batch.step(n_steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def _line(workload, value, ms, steps, warmup, extra):
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms / max(steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": workload}}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_ea3d(args):
+    """3D Edwards-Anderson +-J, L in {4, 6, 8} periodic, 64 disorder realizations per L
+    (couplings iid +-1 from disorder seed 3), R=50000 each, beta 0 -> 3 in 300 steps,
+    theta=10, systematic: 192 runs advanced by the same kernels, steps replayed as graphs."""
+    import torch
+    from paper_2401_07965_gb300 import pa
+    n = 300
+    betas = np.linspace(0.0, 3.0, n + 1)
+    thetas = np.full(n, 10, np.uint32)
+    runs = [{"dim": 3, "L": L, "R": 50000, "couplings": ("ea", 3, 64 * k + r), "ensemble": k}
+            for k, L in enumerate((4, 6, 8)) for r in range(64)]
+    stream = torch.cuda.current_stream()
+    b = pa.Batch(runs, betas, thetas, "systematic", 1000, stream=stream)
+    K = min(args.steps, n - args.warmup)
+    b.step(args.warmup)
+    ms = _timed_batch(pa, b, K, stream)
+    i0, i1 = args.warmup, args.warmup + K
+    upd = float(sum(10 * (L ** 3) * 50000 for L in (4, 6, 8) for _ in range(64)) * K)
+    obs = [b.observables(m) for m in (0, 64, 128)]
+    b.close()
+    _line("3D EA +-J, L=4/6/8 x 64 realizations, R=50000 each, beta 0->3 in 300 steps, "
+          f"theta=10, systematic; timed steps {i0 + 1}..{i1}", upd / (ms * 1e6), ms, K,
+          args.warmup, {"runs": len(runs), "graph": True,
+                        "R_i_check": [o["R_i"] for o in obs]})
+    return 0
+
+
+def run_weighted(args):
+    """2D Ising L=32, beta 0 -> 1 in 150 steps, theta=10, systematic: 256 runs of R=2000 and
+    64 of R=8000 in one batch, combined by Eq. (weighted-averages), against one run of
+    R=1024000.  Whole runs; free energies compared with Kaufman's exact value."""
+    import torch
+    from paper_2401_07965_gb300 import pa
+    L, n = 32, 150
+    betas = np.linspace(0.0, 1.0, n + 1)
+    thetas = np.full(n, 10, np.uint32)
+    stream = torch.cuda.current_stream()
+    runs = [{"dim": 2, "L": L, "R": 2000} for _ in range(256)]
+    runs += [{"dim": 2, "L": L, "R": 8000} for _ in range(64)]
+    exact = _kaufman(L, 1.0)
+    b = pa.Batch(runs, betas, thetas, "systematic", 2000, stream=stream)
+    ms_b = _timed_batch(pa, b, n, stream)
+    w = b.weighted(0)[n]
+    b.close()
+    s = pa.Batch([{"dim": 2, "L": L, "R": 1024000}], betas, thetas, "systematic", 3000,
+                 stream=stream)
+    ms_s = _timed_batch(pa, s, n, stream)
+    mbf_s, _ = s.free_energy(0)
+    s.close()
+    upd = 10.0 * L * L * 1024000 * n
+    _line("weighted averaging: 256 runs R=2000 + 64 runs R=8000 of 2D Ising L=32 (beta 0->1, "
+          "150 steps, theta=10, systematic) in one batch vs one run of R=1024000",
+          upd / (ms_b * 1e6), ms_b, n, 0,
+          {"batch": {"ms": ms_b, "updates_per_ns": upd / (ms_b * 1e6),
+                     "f_err_per_spin": abs(w["minus_beta_F"] - exact) / (L * L),
+                     "weighted_c": w["c"], "naive_c": w["c_naive"], "eff_runs": w["eff_runs"]},
+           "single": {"ms": ms_s, "updates_per_ns": upd / (ms_s * 1e6),
+                      "f_err_per_spin": abs(mbf_s - exact) / (L * L)}})
+    return 0
+
+
+def run_accuracy(args):
+    """Time to a free energy within 1e-4 per spin of Kaufman's value at beta_f = 1 for the
+    benchmark lattice (2D Ising L=64, 200 steps): grid of R and theta, 3 seeds each,
+    systematic; the least GPU time whose worst seed meets the target."""
+    import torch
+    from paper_2401_07965_gb300 import pa
+    L, n = 64, 200
+    betas = np.linspace(0.0, 1.0, n + 1)
+    exact = _kaufman(L, 1.0)
+    stream = torch.cuda.current_stream()
+    grid = []
+    for R in (3000, 10000, 30000, 100000):
+        for theta in (2, 5, 10):
+            errs, times = [], []
+            for seed in (11, 12, 13):
+                b = pa.Batch([{"dim": 2, "L": L, "R": R}], betas, np.full(n, theta, np.uint32),
+                             "systematic", seed, stream=stream)
+                times.append(_timed_batch(pa, b, n, stream))
+                mbf, _ = b.free_energy(0)
+                errs.append(abs(mbf - exact) / (L * L))
+                b.close()
+            grid.append({"R": R, "theta": theta, "ms": float(np.mean(times)),
+                         "max_err_per_spin": float(max(errs))})
+    ok = [g for g in grid if g["max_err_per_spin"] <= 1e-4]
+    best = min(ok, key=lambda g: g["ms"]) if ok else None
+    _line("time to |f - f_exact| <= 1e-4 per spin at beta=1, 2D Ising L=64, 200 steps, "
+          "systematic, 3 seeds", best["ms"] if best else None, best["ms"] if best else 0.0,
+          n, 0, {"unit": "ms", "higher_is_better": False, "best": best, "grid": grid})
+    return 0
+
+
 def run_e2e(args, pa, stream, seed, dev, threads=0):
     """Whole runs through the C ABI: host schedule -> pa_init -> per step pa_step +
     pa_observables (device -> host) -> pa_free_energy.  Host wall clock."""
@@ -416,6 +540,10 @@ def main():
     ap.add_argument("--threads", type=int, default=0, help="small case: sweep threads per CTA")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: one run of R=20000 replicas of the same lattice (profiling)")
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "ea3d", "weighted", "accuracy"],
+                    help="headline: the benchmark line; ea3d / weighted: the batched "
+                         "workloads; accuracy: time to a free energy within 1e-4 per spin")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -423,6 +551,12 @@ def main():
         return run_reference(args)
     if args.case == "small":
         return run_small(args)
+    if args.workload == "ea3d":
+        return run_ea3d(args)
+    if args.workload == "weighted":
+        return run_weighted(args)
+    if args.workload == "accuracy":
+        return run_accuracy(args)
     return run_ours(args)
 
 
