@@ -490,6 +490,132 @@ def run_accuracy(args):
     return 0
 
 
+def _chunked(pa, pop, stream, n_max, chunk=16):
+    """Advance a run in chunks of steps until n_max steps or, under the controller, until
+    beta_f; device time summed over the chunks (CUDA events on the run's stream)."""
+    import torch
+    ms = 0.0
+    done = 0
+    while done < n_max:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = min(chunk, n_max - done)
+        a.record(stream)
+        try:
+            pop.step(k)
+        except pa.PAError as e:
+            if e.status != pa.PA_ERR_DONE:
+                raise
+            b.record(stream)
+            torch.cuda.synchronize()
+            break
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+        done += k
+        pa.pa_sync(pop.ctx)
+    return ms
+
+
+def _schedule_arm(pa, CT, sysdef, seeds, stream, plain=None, learned=None, bits=None):
+    """Runs of one schedule over seeds: plain = (n_steps, theta); learned = (grid points K,
+    plain_units, plain_theta, budget).  Returns per-seed -beta F, e, rho_t / R, ms, steps."""
+    dim, L, cpl, R, bf = sysdef
+    out = []
+    for seed in seeds:
+        if plain:
+            n, theta = plain
+            pop = pa.Population(dim, L, R, np.linspace(0.0, bf, n + 1),
+                                np.full(n, theta, np.uint32), "systematic", seed,
+                                couplings=cpl, stream=stream)
+            ms = _chunked(pa, pop, stream, n)
+            sweeps = n * theta
+        else:
+            K, units, theta, budget = learned
+            pop = CT.controlled_run(dim, L, cpl, R, np.linspace(0.0, bf, K + 1), units, theta,
+                                    bits, seed=seed, budget=budget, stream=stream)
+            ms = _chunked(pa, pop, stream, K)
+            _, th = pa.pa_schedule_taken(pop.ctx, K + 1)
+            sweeps = int(th.sum())
+        o = pop.observables()
+        out.append({"mbf": L ** dim * math.log(2.0) + o["sum_lnQ"], "e": o["e"],
+                    "rho": o["rho_t"] / R, "ms": ms, "steps": o["step"], "sweeps": sweeps})
+        pop.close()
+    return out
+
+
+def _summ(rows, ref_mbf, ref_e, N):
+    err = np.array([(r["mbf"] - ref_mbf) / N for r in rows])
+    out = {"rms_f_err_per_spin": float(np.sqrt(np.mean(err ** 2))),
+           "mean_f_err_per_spin": float(err.mean()),
+           "rho_t_over_R": float(np.mean([r["rho"] for r in rows])),
+           "ms": float(np.mean([r["ms"] for r in rows])),
+           "steps": float(np.mean([r["steps"] for r in rows])),
+           "sweeps": float(np.mean([r["sweeps"] for r in rows])), "seeds": len(rows)}
+    if ref_e is not None:
+        out["rms_e_err"] = float(np.sqrt(np.mean([(r["e"] - ref_e) ** 2 for r in rows])))
+    return out
+
+
+def run_controller(args):
+    """The learned schedule controller against the plain schedule.
+
+    3D +-J spin glass L=10 (disorder seed 5, realization 0), R=100000, beta 0 -> 3: plain 300
+    steps of 10 sweeps against the learned schedule on a 600-point grid with the same 3000
+    sweeps, and with 2250 and 1500; errors against one R=10^6 run (600 steps, 30 sweeps).
+    2D Ising L=64, R=10000, beta 0 -> 1: plain 200 steps of 10 sweeps against the learned
+    schedule on an 800-point grid with 2000, 1500 and 1000 sweeps; errors against Kaufman's
+    exact free energy.  Value: device time of the cheapest learned schedule whose
+    root-mean-square free-energy error is at most the plain schedule's (spin glass)."""
+    import torch
+    from paper_2401_07965_gb300 import controller as CT
+    from paper_2401_07965_gb300 import pa
+    if not os.path.exists(CT.WEIGHTS):
+        print(json.dumps({"metric": METRIC, "value": None, "unavailable":
+                          "no trained controller weights"}), flush=True)
+        return 1
+    bits = CT.load()
+    stream = torch.cuda.Stream()
+    S = args.seeds
+    seeds = range(1, S + 1)
+    res = {}
+    # spin glass, config of the learned-schedule benchmark
+    ea = (3, 10, ("ea", 5, 0), 100000, 3.0)
+    ref = _schedule_arm(pa, CT, (3, 10, ("ea", 5, 0), 1000000, 3.0), [4242], stream,
+                        plain=(600, 30))[0]
+    N = 1000
+    res["ea10"] = {"reference": {"R": 1000000, "steps": 600, "theta": 30, "mbf": ref["mbf"],
+                                 "e": ref["e"], "ms": ref["ms"]}}
+    res["ea10"]["plain"] = _summ(_schedule_arm(pa, CT, ea, seeds, stream, plain=(300, 10)),
+                                 ref["mbf"], ref["e"], N)
+    for budget in (3000, 2250, 1500):
+        res["ea10"][f"learned_{budget}"] = _summ(
+            _schedule_arm(pa, CT, ea, seeds, stream, learned=(600, 2, 10, budget), bits=bits),
+            ref["mbf"], ref["e"], N)
+    # 2D Ising, exact reference
+    L = 64
+    exact = _kaufman(L, 1.0)
+    ising = (2, L, ("ferro",), 10000, 1.0)
+    res["ising64"] = {"plain": _summ(_schedule_arm(pa, CT, ising, seeds, stream,
+                                                   plain=(200, 10)), exact, None, L * L)}
+    for budget in (2000, 1500, 1000):
+        res["ising64"][f"learned_{budget}"] = _summ(
+            _schedule_arm(pa, CT, ising, seeds, stream, learned=(800, 4, 10, budget), bits=bits),
+            exact, None, L * L)
+    p_ea = res["ea10"]["plain"]
+    ok = [res["ea10"][f"learned_{b}"] for b in (3000, 2250, 1500)
+          if res["ea10"][f"learned_{b}"]["rms_f_err_per_spin"] <= p_ea["rms_f_err_per_spin"]]
+    best = min(ok, key=lambda r: r["ms"]) if ok else None
+    _line("learned vs plain schedule: 3D EA +-J L=10, R=100000, beta 0->3, plain 300 steps x "
+          "10 sweeps vs learned on a 600-point grid at 3000/2250/1500 sweeps; 2D Ising L=64, "
+          f"R=10000, beta 0->1 vs Kaufman; {S} seeds each",
+          best["ms"] if best else None, best["ms"] if best else 0.0, 0, 0,
+          {"unit": "ms", "higher_is_better": False,
+           "what": "device ms per run of the cheapest learned schedule whose rms free-energy "
+                   "error (3D EA L=10) is at most the plain 3000-sweep schedule's",
+           "plain_ms": p_ea["ms"], "results": res})
+    return 0
+
+
 def run_e2e(args, pa, stream, seed, dev, threads=0):
     """Whole runs through the C ABI: host schedule -> pa_init -> per step pa_step +
     pa_observables (device -> host) -> pa_free_energy.  Host wall clock."""
@@ -538,12 +664,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--threads", type=int, default=0, help="small case: sweep threads per CTA")
+    ap.add_argument("--seeds", type=int, default=24, help="controller workload: seeds per arm")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: one run of R=20000 replicas of the same lattice (profiling)")
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "ea3d", "weighted", "accuracy"],
+                    choices=["headline", "ea3d", "weighted", "accuracy", "controller"],
                     help="headline: the benchmark line; ea3d / weighted: the batched "
-                         "workloads; accuracy: time to a free energy within 1e-4 per spin")
+                         "workloads; accuracy: time to a free energy within 1e-4 per spin; "
+                         "controller: learned against plain schedule")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -557,6 +685,8 @@ def main():
         return run_weighted(args)
     if args.workload == "accuracy":
         return run_accuracy(args)
+    if args.workload == "controller":
+        return run_controller(args)
     return run_ours(args)
 
 

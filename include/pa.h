@@ -115,6 +115,9 @@ typedef struct {
     double chi;            /* susceptibility per spin beta N (<m^2> - <|m|>^2)        */
     double rho_t;          /* family statistic of Eq. (rho_t), sum c_k^2 / R_i       */
     double accept_rate;    /* accepts / (theta_i N R_i)                             */
+    float features[8];     /* learned schedule: the controller's inputs after step i */
+    int32_t u_next;        /* its choice for step i+1: grid points (0 = none) ...   */
+    uint32_t theta_next;   /* ... and sweeps                                        */
 } pa_obs;
 
 /* One run of a batch (pa_batch_init).  All runs of a batch share the
@@ -291,6 +294,61 @@ pa_status pa_weighted(pa_ctx *ctx, int32_t ensemble, pa_weighted_obs *rows, int3
 /* Replay each temperature step as one captured CUDA graph (default on; needs a
  * non-NULL stream; timing mode launches directly). */
 pa_status pa_set_graph(pa_ctx *ctx, int32_t on);
+
+/* ---- learned schedule -----------------------------------------------------
+ *
+ * Adaptive temperature steps and sweep numbers (cited in Sec. 5 of the paper as
+ * established practice) chosen by a small network after every step.  The
+ * schedule given to pa_init becomes a grid: beta may only take its values
+ * beta[0..K] (K = n_steps), a step advances u = 1..u_max grid points, and the
+ * sweeps of all steps together stay within `budget`.  After each step a kernel
+ * reads the population statistics (beta, <E>/N, var(E)/N, ln Q, rho_t,
+ * family entropy, acceptance rate, L), evaluates an 8 -> 64 -> 64 -> 2 ReLU
+ * network with BF16 parameters and FP32 accumulation, and writes the next
+ * step's entries into the step tables: outputs s (step relative to the
+ * average remaining step) and t (sweeps relative to budget / planned steps).
+ * Non-finite or out-of-range outputs, or use_mlp = 0, take the plain step
+ * (plain_units, plain_theta).  When beta reaches beta[K] the run finishes:
+ * later pa_step calls launch nothing useful and pa_sync reports PA_OK.
+ * Only for single-run contexts, before the first pa_step. */
+#define PA_MLP_IN 8
+#define PA_MLP_HIDDEN 64
+#define PA_MLP_OUT 2
+/* parameters in this order: W1[64][8], b1[64], W2[64][64], b2[64], W3[2][64], b3[2] */
+#define PA_MLP_NPARAM 4866
+
+typedef struct {
+    const uint16_t *params;   /* host, PA_MLP_NPARAM BF16 values; NULL with use_mlp = 0 */
+    int32_t use_mlp;
+    int32_t plain_units;      /* grid points per plain step                          */
+    uint32_t plain_theta;     /* sweeps per plain step                               */
+    uint32_t theta_min, theta_max;
+    uint32_t budget;          /* total sweeps; 0 = plain_theta * K / plain_units     */
+    int32_t u_max;            /* largest step in grid points, 1..8                   */
+} pa_controller;
+
+pa_status pa_set_controller(pa_ctx *ctx, const pa_controller *cfg);
+
+/* Synchronise and copy the schedule taken so far: beta[0..step] (host, step+1
+ * values) and theta[0..step-1]; *n receives step + 1. */
+pa_status pa_schedule_taken(pa_ctx *ctx, double *beta, uint32_t *theta, int32_t max,
+                            int32_t *n);
+
+/* Training of the network on the device (stateless; all pointers device).
+ * X [B][8] features, Yt [B][2] targets, mask [B][2] weights of the squared
+ * errors; params [PA_MLP_NPARAM] FP32 master values (the forward pass rounds
+ * them to BF16 as inference does).  pa_mlp_gradients writes d(loss)/d(params)
+ * with loss = sum mask (y - yt)^2 / (2B); scratch holds pa_mlp_scratch_bytes(B)
+ * bytes.  pa_mlp_adam applies one Adam step (step >= 1) and refreshes the BF16
+ * copy when params_bf16 != NULL.  pa_mlp_forward evaluates BF16 parameters. */
+size_t pa_mlp_scratch_bytes(int32_t B);
+pa_status pa_mlp_forward(const uint16_t *params_bf16, const float *X, int32_t B, float *Y,
+                         void *cuda_stream);
+pa_status pa_mlp_gradients(const float *params, const float *X, const float *Yt,
+                           const float *mask, int32_t B, float *grads, float *loss,
+                           void *scratch, size_t scratch_bytes, void *cuda_stream);
+pa_status pa_mlp_adam(float *params, const float *grads, float *m, float *v,
+                      uint16_t *params_bf16, int32_t step, float lr, void *cuda_stream);
 
 /* Release the context (and the device memory it allocated).  NULL is a no-op. */
 pa_status pa_destroy(pa_ctx *ctx);

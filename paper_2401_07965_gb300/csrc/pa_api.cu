@@ -34,7 +34,10 @@ enum Region {
     R_PA, R_PB, R_OA, R_OB, R_PD, R_PCL, R_JB, R_ST, R_TRACE, R_COUNT
 };
 
-enum Shared { S_RUNS, S_B2R, S_G2R, S_BETA, S_DBETA, S_Q, S_THR, S_THETA, S_IDS, S_WOUT, S_COUNT };
+enum Shared {
+    S_RUNS, S_B2R, S_G2R, S_BETA, S_DBETA, S_Q, S_THR, S_THETA, S_IDS, S_WOUT,
+    S_CTL, S_GBETA, S_GTHR, S_GDB, S_GQ, S_COUNT
+};
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -71,6 +74,13 @@ struct pa_ctx {
     std::vector<uint32_t> theta;
     int32_t* d_ids = nullptr;               // run index list for pa_weighted (device)
     pa_weighted_obs* d_wout = nullptr;      // its output rows (device)
+    bool controlled = false;                // learned schedule active
+    bool finished = false;                  // beta_f reached under the controller
+    CtlDev* d_ctl = nullptr;
+    double* d_gbeta = nullptr;
+    uint32_t* d_gthr = nullptr;
+    double* d_gdb = nullptr;
+    double* d_gq = nullptr;
 };
 
 namespace {
@@ -144,6 +154,10 @@ Layout make_layout(const std::vector<RunHost>& runs, int n_steps) {
     sz[S_THETA] = (size_t)n_steps * 4;
     sz[S_IDS] = M * 4;
     sz[S_WOUT] = (size_t)(n_steps + 1) * sizeof(pa_weighted_obs);
+    sz[S_CTL] = sizeof(CtlDev);
+    sz[S_GBETA] = (size_t)(n_steps + 1) * 8;
+    sz[S_GTHR] = (size_t)(n_steps + 1) * 16;
+    sz[S_GDB] = sz[S_GQ] = (size_t)(n_steps + 1) * CTL_UMAX * 8;
     size_t o = 0;
     for (int r = 0; r < S_COUNT; ++r) {
         L.shared_off[r] = o;
@@ -281,14 +295,41 @@ void fill_obs(const pa_ctx* ctx, int run, const TraceRow& t, int step, pa_obs* o
     o->rho_t = (double)o->sumC2 / R;
     const double th = step > 0 ? (double)ctx->theta[step - 1] : 0.0;
     o->accept_rate = th > 0 ? (double)o->accepts / (th * N * R) : 0.0;
+    for (int k = 0; k < 8; ++k) o->features[k] = t.x[k];
+    o->u_next = t.u_next;
+    o->theta_next = t.theta_next;
 }
 
-// all kernels of one temperature step
+// all kernels of one temperature step (and the controller's choice of the next)
 pa_status enqueue_step(pa_ctx* ctx, int64_t* launches) {
     PA_CUDA(launch_resample(ctx->kp, ctx->stream, launches));
     PA_CUDA(launch_sweep(ctx->kp, ctx->threads, ctx->stream));
     if (launches) *launches += 1;
     PA_CUDA(launch_family_finish(ctx->kp, 0, ctx->stream, launches));
+    if (ctx->controlled) {
+        PA_CUDA(launch_control(ctx->kp, ctx->stream));
+        if (launches) *launches += 1;
+    }
+    return PA_OK;
+}
+
+// Metropolis thresholds at beta: floor(2^32 exp(-4 k beta)), k = 1..3
+void thresholds_at(double beta, uint32_t out[4]) {
+    out[0] = 0xFFFFFFFFu;
+    for (int k = 1; k < 4; ++k) {
+        const double x = beta * (double)(4 * k);
+        const double t = std::ldexp(std::exp(-x), 32);
+        out[k] = (t >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)std::floor(t);
+    }
+}
+
+// copy the step tables written by the controller back to the host
+pa_status refresh_schedule(pa_ctx* ctx) {
+    const int n = ctx->n_steps;
+    PA_CUDA(cudaMemcpy(ctx->beta.data(), ctx->kp.beta, sizeof(double) * (n + 1),
+                       cudaMemcpyDeviceToHost));
+    PA_CUDA(cudaMemcpy(ctx->theta.data(), ctx->kp.theta, sizeof(uint32_t) * n,
+                       cudaMemcpyDeviceToHost));
     return PA_OK;
 }
 
@@ -434,6 +475,17 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     p.theta = (const uint32_t*)(base + lay.shared_off[S_THETA]);
     ctx->d_ids = (int32_t*)(base + lay.shared_off[S_IDS]);
     ctx->d_wout = (pa_weighted_obs*)(base + lay.shared_off[S_WOUT]);
+    p.beta_rw = (double*)p.beta;
+    p.dbeta_rw = (double*)p.dbeta;
+    p.q_rw = (double*)p.q;
+    p.thr_rw = (uint32_t*)p.thr;
+    p.theta_rw = (uint32_t*)p.theta;
+    p.ctl = nullptr;
+    ctx->d_ctl = (CtlDev*)(base + lay.shared_off[S_CTL]);
+    ctx->d_gbeta = (double*)(base + lay.shared_off[S_GBETA]);
+    ctx->d_gthr = (uint32_t*)(base + lay.shared_off[S_GTHR]);
+    ctx->d_gdb = (double*)(base + lay.shared_off[S_GDB]);
+    ctx->d_gq = (double*)(base + lay.shared_off[S_GQ]);
 
     // per-run descriptors and block -> run maps
     std::vector<uint32_t> b2r, g2r;
@@ -497,12 +549,7 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     for (int i = 1; i <= n; ++i) {
         dbeta[i - 1] = ctx->beta[i] - ctx->beta[i - 1];
         q[i - 1] = std::exp(-(4.0 * dbeta[i - 1]));
-        thr[4 * (i - 1)] = 0xFFFFFFFFu;
-        for (int k = 1; k < 4; ++k) {
-            const double x = ctx->beta[i] * (double)(4 * k);
-            const double t = std::ldexp(std::exp(-x), 32);
-            thr[4 * (i - 1) + k] = (t >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)std::floor(t);
-        }
+        thresholds_at(ctx->beta[i], &thr[4 * (i - 1)]);
     }
 
     cudaError_t e = cudaSuccess;
@@ -569,6 +616,12 @@ int32_t pa_batch_size(const pa_ctx* ctx) { return ctx ? ctx->M : 0; }
 pa_status pa_step(pa_ctx* ctx, int32_t n) {
     if (!ctx || n < 0) return PA_ERR_ARG;
     if (ctx->sticky != PA_OK) return PA_ERR_STATE;
+    if (ctx->controlled) {
+        // the number of steps to beta_f is chosen on the device; steps launched
+        // after it is reached return at once
+        if (ctx->finished) return PA_ERR_DONE;
+        if (ctx->host_step + n > ctx->n_steps) n = ctx->n_steps - ctx->host_step;
+    }
     if (ctx->host_step + n > ctx->n_steps) return PA_ERR_DONE;
     const bool graph = ctx->use_graph && !ctx->timing && ctx->stream != nullptr;
     if (graph && n > 0 && (!ctx->graph || ctx->graph_threads != ctx->threads)) {
@@ -593,6 +646,10 @@ pa_status pa_step(pa_ctx* ctx, int32_t n) {
             ctx->launches += 1;
             PA_CUDA(cudaEventRecord(b, ctx->stream));
             PA_CUDA(launch_family_finish(ctx->kp, 0, ctx->stream, &ctx->launches));
+            if (ctx->controlled) {
+                PA_CUDA(launch_control(ctx->kp, ctx->stream));
+                ctx->launches += 1;
+            }
         } else {
             const pa_status s = enqueue_step(ctx, &ctx->launches);
             if (s != PA_OK) return s;
@@ -609,12 +666,20 @@ pa_status pa_sync(pa_ctx* ctx) {
     for (int m = 0; m < ctx->M; ++m) {
         DevState st;
         PA_CUDA(cudaMemcpy(&st, ctx->desc[m].st, sizeof(DevState), cudaMemcpyDeviceToHost));
+        if (ctx->controlled) {
+            ctx->host_step = st.step;
+            if (st.status == S_DONE) {
+                ctx->finished = true;
+                st.status = S_OK;
+            }
+        }
         const pa_status s = map_dev_status(st.status);
         if (s != PA_OK) {
             ctx->sticky = s;
             return s;
         }
     }
+    if (ctx->controlled) return refresh_schedule(ctx);
     return PA_OK;
 }
 
@@ -781,6 +846,78 @@ pa_status pa_weighted(pa_ctx* ctx, int32_t ensemble, pa_weighted_obs* rows, int3
                            cudaMemcpyDeviceToHost));
     }
     if (n_rows) *n_rows = n;
+    return PA_OK;
+}
+
+pa_status pa_set_controller(pa_ctx* ctx, const pa_controller* cfg) {
+    if (!ctx || !cfg || ctx->M != 1 || ctx->host_step != 0 || ctx->controlled) return PA_ERR_ARG;
+    if (ctx->sticky != PA_OK) return PA_ERR_STATE;
+    const int K = ctx->n_steps;
+    if (cfg->u_max < 1 || cfg->u_max > CTL_UMAX || cfg->plain_units < 1 ||
+        cfg->plain_units > cfg->u_max || cfg->theta_min > cfg->theta_max ||
+        cfg->theta_max >= (1u << 24) || cfg->plain_theta >= (1u << 24) ||
+        (cfg->use_mlp && !cfg->params))
+        return PA_ERR_ARG;
+    CtlDev c;
+    std::memset(&c, 0, sizeof(c));
+    if (cfg->params) std::memcpy(c.w, cfg->params, sizeof(c.w));
+    c.use_mlp = cfg->use_mlp ? 1 : 0;
+    c.K = K;
+    c.plain_units = cfg->plain_units;
+    c.plain_theta = cfg->plain_theta;
+    c.theta_min = cfg->theta_min;
+    c.theta_max = cfg->theta_max;
+    const int planned = (K + cfg->plain_units - 1) / cfg->plain_units;
+    c.budget = cfg->budget ? cfg->budget : cfg->plain_theta * (uint32_t)planned;
+    c.u_max = cfg->u_max;
+    c.theta_c = (float)c.budget / (float)planned;
+    c.beta_grid = ctx->d_gbeta;
+    c.thr_grid = ctx->d_gthr;
+    c.dbeta_tab = ctx->d_gdb;
+    c.q_tab = ctx->d_gq;
+    // grid tables: beta_k, thresholds at beta_k, and for each step of u points
+    // dbeta = beta_{k+u} - beta_k with q = exp(-4 dbeta)
+    std::vector<uint32_t> gthr((size_t)4 * (K + 1));
+    std::vector<double> gdb((size_t)(K + 1) * CTL_UMAX, 0.0), gq((size_t)(K + 1) * CTL_UMAX, 1.0);
+    for (int k = 0; k <= K; ++k) {
+        thresholds_at(ctx->beta[k], &gthr[4 * k]);
+        for (int u = 1; u <= CTL_UMAX && k + u <= K; ++u) {
+            const double db = ctx->beta[k + u] - ctx->beta[k];
+            gdb[(size_t)k * CTL_UMAX + u - 1] = db;
+            gq[(size_t)k * CTL_UMAX + u - 1] = std::exp(-(4.0 * db));
+        }
+    }
+    PA_CUDA(cudaStreamSynchronize(ctx->stream));
+    PA_CUDA(cudaMemcpy(ctx->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(ctx->d_gbeta, ctx->beta.data(), sizeof(double) * (K + 1),
+                       cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(ctx->d_gthr, gthr.data(), gthr.size() * 4, cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(ctx->d_gdb, gdb.data(), gdb.size() * 8, cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(ctx->d_gq, gq.data(), gq.size() * 8, cudaMemcpyHostToDevice));
+    ctx->kp.ctl = ctx->d_ctl;
+    ctx->controlled = true;
+    if (ctx->graph) {  // the step graph must now include the controller
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    // choose the first step from the initial population
+    PA_CUDA(launch_control(ctx->kp, ctx->stream));
+    ctx->launches += 1;
+    return pa_sync(ctx);
+}
+
+pa_status pa_schedule_taken(pa_ctx* ctx, double* beta, uint32_t* theta, int32_t max,
+                            int32_t* n) {
+    if (!ctx || max < 0) return PA_ERR_ARG;
+    pa_status s = pa_sync(ctx);
+    if (s != PA_OK) return s;
+    int cnt = ctx->host_step + 1;
+    if (cnt > max) cnt = max;
+    for (int i = 0; i < cnt; ++i) {
+        if (beta) beta[i] = ctx->beta[i];
+        if (theta && i > 0) theta[i - 1] = ctx->theta[i - 1];
+    }
+    if (n) *n = cnt;
     return PA_OK;
 }
 

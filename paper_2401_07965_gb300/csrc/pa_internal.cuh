@@ -39,7 +39,30 @@ constexpr uint32_t POISSON_KMAX = 256; // per chunk of mean <= 16
 
 enum Method { M_MULTINOMIAL = 0, M_SYSTEMATIC = 1, M_RESIDUAL = 2, M_POISSON = 3, M_NEAREST = 4 };
 
-enum DevStatus { S_OK = 0, S_CAPACITY = 4, S_KMAX = 5, S_TIMEOUT = 6 };
+enum DevStatus { S_OK = 0, S_CAPACITY = 4, S_KMAX = 5, S_TIMEOUT = 6, S_DONE = 8 };
+
+// learned-schedule controller (MLP 8 -> 64 -> 64 -> 2, BF16 parameters)
+constexpr int MLP_IN = 8, MLP_HID = 64, MLP_OUT = 2;
+constexpr int MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID +
+                           MLP_OUT * MLP_HID + MLP_OUT;
+constexpr int CTL_UMAX = 8;  // largest step in grid units
+
+struct CtlDev {
+    uint16_t w[MLP_NPARAM];      // BF16 parameters: W1, b1, W2, b2, W3, b3
+    int32_t use_mlp;             // 0: plain steps of plain_units with plain_theta
+    int32_t K;                   // grid index of beta_f
+    int32_t plain_units;
+    uint32_t plain_theta;
+    uint32_t theta_min, theta_max;
+    uint32_t budget;             // total sweeps
+    int32_t u_max;               // <= CTL_UMAX
+    float theta_c;               // sweeps per step of the planned step count
+    int32_t pad[3];
+    const double* beta_grid;     // K + 1
+    const uint32_t* thr_grid;    // 4 per grid point
+    const double* dbeta_tab;     // (K + 1) x CTL_UMAX: beta[k+u] - beta[k]
+    const double* q_tab;         // exp(-4 dbeta_tab)
+};
 
 struct uint4x {
     uint32_t x, y, z, w;
@@ -83,7 +106,9 @@ struct DevState {
     uint64_t T;        // sum of fixed-point weights f_j
     uint64_t Tres;     // sum of their fractional parts (residual rule)
     uint64_t Rres;     // residual draws
-    uint64_t pad[2];
+    int32_t kgrid;     // learned schedule: grid index of the current beta
+    uint32_t sweeps;   // learned schedule: sweeps spent so far
+    uint64_t pad;
 };
 
 // Per-step accumulators, device-resident (row i = after temperature step i).
@@ -94,7 +119,9 @@ struct TraceRow {
     double sv_sum;   // sum_j (r_j - f_j 2^-40)^2 over parents
     unsigned long long sumE, sumE2, sumAbsM, sumM2, sumC2, accepts;  // two's complement
     uint32_t R_i, R_prev;
-    uint64_t pad;
+    float x[8];       // learned schedule: features seen by the controller after this step
+    int32_t u_next;   // its choice: grid units of the next step (0 = none)
+    uint32_t theta_next;  // and the sweeps of the next step
 };
 
 // Per-run description, in device memory (one per run of the batch).
@@ -146,6 +173,12 @@ struct KParams {
     const double* q;         // exp(-4 dbeta), n_steps
     const uint32_t* thr;     // 4 per step (index 1..d used)
     const uint32_t* theta;   // n_steps
+    double* beta_rw;         // the same tables, written by the learned-schedule controller
+    double* dbeta_rw;
+    double* q_rw;
+    uint32_t* thr_rw;
+    uint32_t* theta_rw;
+    const CtlDev* ctl;       // null without a controller
 };
 
 constexpr int SCAN_THREADS = 256;
@@ -162,6 +195,7 @@ cudaError_t launch_resample(const KParams& p, cudaStream_t s, int64_t* launches)
 cudaError_t launch_sweep(const KParams& p, int threads, cudaStream_t s);
 cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int64_t* launches);
 cudaError_t prepare_sweep(const KParams& p, int threads);
+cudaError_t launch_control(const KParams& p, cudaStream_t s);
 int sweep_threads(int N);
 bool sweep_threads_supported(int t);
 }  // namespace pa

@@ -33,7 +33,8 @@ EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observable
            "pa_weights_static", "pa_set_sweep_threads", "pa_get_sweep_threads",
            "pa_batch_workspace_bytes", "pa_batch_init", "pa_batch_size", "pa_run_observables",
            "pa_run_trace", "pa_run_free_energy", "pa_run_get_array", "pa_weighted",
-           "pa_set_graph"]
+           "pa_set_graph", "pa_set_controller", "pa_schedule_taken", "pa_mlp_scratch_bytes",
+           "pa_mlp_forward", "pa_mlp_gradients", "pa_mlp_adam"]
 
 
 class pa_lattice(C.Structure):
@@ -58,10 +59,13 @@ class pa_obs(C.Structure):
                 ("accepts", C.c_uint64), ("entropy", C.c_double), ("sv", C.c_double),
                 ("e", C.c_double), ("e2", C.c_double), ("absm", C.c_double), ("m2", C.c_double),
                 ("c", C.c_double), ("chi", C.c_double), ("rho_t", C.c_double),
-                ("accept_rate", C.c_double)]
+                ("accept_rate", C.c_double), ("features", C.c_float * 8),
+                ("u_next", C.c_int32), ("theta_next", C.c_uint32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad0"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad0", "features")}
+        d["features"] = list(self.features)
+        return d
 
 
 class pa_run_spec(C.Structure):
@@ -79,6 +83,16 @@ class pa_weighted_obs(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PA_MLP_NPARAM = 4866
+
+
+class pa_controller(C.Structure):
+    _fields_ = [("params", C.POINTER(C.c_uint16)), ("use_mlp", C.c_int32),
+                ("plain_units", C.c_int32), ("plain_theta", C.c_uint32),
+                ("theta_min", C.c_uint32), ("theta_max", C.c_uint32), ("budget", C.c_uint32),
+                ("u_max", C.c_int32)]
 
 
 class PAError(RuntimeError):
@@ -131,6 +145,14 @@ def _load():
     lib.pa_weighted.argtypes = [vp, C.c_int32, C.POINTER(pa_weighted_obs), C.c_int32,
                                 C.POINTER(C.c_int32)]
     lib.pa_set_graph.argtypes = [vp, C.c_int32]
+    lib.pa_set_controller.argtypes = [vp, C.POINTER(pa_controller)]
+    lib.pa_schedule_taken.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint32),
+                                      C.c_int32, C.POINTER(C.c_int32)]
+    lib.pa_mlp_scratch_bytes.argtypes = [C.c_int32]
+    lib.pa_mlp_scratch_bytes.restype = sz
+    lib.pa_mlp_forward.argtypes = [vp, vp, C.c_int32, vp, vp]
+    lib.pa_mlp_gradients.argtypes = [vp, vp, vp, vp, C.c_int32, vp, vp, vp, sz, vp]
+    lib.pa_mlp_adam.argtypes = [vp, vp, vp, vp, vp, C.c_int32, C.c_float, vp]
     lib.pa_set_sweep_threads.argtypes = [vp, C.c_int32]
     lib.pa_get_sweep_threads.argtypes = [vp]
     lib.pa_get_sweep_threads.restype = C.c_int32
@@ -138,7 +160,8 @@ def _load():
     lib.pa_strerror.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("pa_workspace_bytes", "pa_launch_count", "pa_strerror",
-                        "pa_get_sweep_threads", "pa_batch_workspace_bytes", "pa_batch_size"):
+                        "pa_get_sweep_threads", "pa_batch_workspace_bytes", "pa_batch_size",
+                        "pa_mlp_scratch_bytes"):
             getattr(lib, name).restype = C.c_int
     return lib
 
@@ -350,6 +373,48 @@ def pa_weighted(ctx, ensemble, max_rows) -> list:
 
 def pa_set_graph(ctx, on=True):
     _check(_lib.pa_set_graph(ctx, 1 if on else 0), "pa_set_graph")
+
+
+def pa_set_controller(ctx, params_bf16, use_mlp, plain_units, plain_theta, theta_min,
+                      theta_max, budget, u_max):
+    bits = None if params_bf16 is None else np.ascontiguousarray(params_bf16, np.uint16)
+    cfg = pa_controller(None if bits is None else bits.ctypes.data_as(C.POINTER(C.c_uint16)),
+                        int(use_mlp), int(plain_units), int(plain_theta), int(theta_min),
+                        int(theta_max), int(budget), int(u_max))
+    _check(_lib.pa_set_controller(ctx, C.byref(cfg)), "pa_set_controller")
+
+
+def pa_schedule_taken(ctx, max_rows):
+    b = np.zeros(max_rows, np.float64)
+    t = np.zeros(max(max_rows - 1, 1), np.uint32)
+    n = C.c_int32()
+    _check(_lib.pa_schedule_taken(ctx, b.ctypes.data_as(C.POINTER(C.c_double)),
+                                  t.ctypes.data_as(C.POINTER(C.c_uint32)), max_rows, C.byref(n)),
+           "pa_schedule_taken")
+    return b[: n.value], t[: max(n.value - 1, 0)]
+
+
+def pa_mlp_scratch_bytes(B) -> int:
+    return int(_lib.pa_mlp_scratch_bytes(int(B)))
+
+
+def pa_mlp_forward(params_bf16_ptr, X_ptr, B, Y_ptr, stream=0):
+    _check(_lib.pa_mlp_forward(C.c_void_p(params_bf16_ptr), C.c_void_p(X_ptr), int(B),
+                               C.c_void_p(Y_ptr), C.c_void_p(stream)), "pa_mlp_forward")
+
+
+def pa_mlp_gradients(params_ptr, X_ptr, Yt_ptr, mask_ptr, B, grads_ptr, loss_ptr, scratch_ptr,
+                     scratch_bytes, stream=0):
+    _check(_lib.pa_mlp_gradients(C.c_void_p(params_ptr), C.c_void_p(X_ptr), C.c_void_p(Yt_ptr),
+                                 C.c_void_p(mask_ptr), int(B), C.c_void_p(grads_ptr),
+                                 C.c_void_p(loss_ptr), C.c_void_p(scratch_ptr),
+                                 int(scratch_bytes), C.c_void_p(stream)), "pa_mlp_gradients")
+
+
+def pa_mlp_adam(params_ptr, grads_ptr, m_ptr, v_ptr, params_bf16_ptr, step, lr, stream=0):
+    _check(_lib.pa_mlp_adam(C.c_void_p(params_ptr), C.c_void_p(grads_ptr), C.c_void_p(m_ptr),
+                            C.c_void_p(v_ptr), C.c_void_p(params_bf16_ptr), int(step),
+                            float(lr), C.c_void_p(stream)), "pa_mlp_adam")
 
 
 def pa_destroy(ctx):
