@@ -204,6 +204,23 @@ def run_reference(args):
     return 0
 
 
+def combine_over_ranks(ms, units, device):
+    """Whole-job figures of independent runs on several ranks: the maximum of the ranks'
+    device times and the sum of their units (one all-reduce each; no data-path exchange)."""
+    import torch
+    import torch.distributed as dist
+    t_ms = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    t_units = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t_units, op=dist.ReduceOp.SUM)
+    return float(t_ms[0]), float(t_units[0])
+
+
+def rank_seed(rank):
+    """Each rank runs its own population: the Philox key is offset by the rank."""
+    return SEED + 1000 * rank
+
+
 # ----------------------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------------------
@@ -220,7 +237,7 @@ def run_ours(args):
 
     betas = np.linspace(0.0, BETA_F, NSTEPS + 1)
     thetas = np.full(NSTEPS, THETA, np.uint32)
-    seed = SEED + 1000 * rank
+    seed = rank_seed(rank)
     stream = torch.cuda.current_stream(dev)
 
     # launch configuration of the sweep from the autotuner (timed on this GPU, cached)
@@ -283,11 +300,7 @@ def run_ours(args):
     total_ms = sum(step_ms)
     # max over ranks of the device time; sum of the units
     if world > 1:
-        t = torch.tensor([total_ms, updates], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        total_ms, updates = float(mx[0]), float(t[1])
+        total_ms, updates = combine_over_ranks(total_ms, updates, dev)
     value = updates / (total_ms * 1e6)
     for p in runs:
         p.close()
