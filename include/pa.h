@@ -222,7 +222,7 @@ pa_status pa_sweep_timing(pa_ctx *ctx, double *ms, int64_t *launches, double *up
 /* Number of kernels this context has launched so far. */
 int64_t pa_launch_count(const pa_ctx *ctx);
 
-/* Launch configuration of the sweep kernel: threads per CTA (64, 128, 256 or
+/* Launch configuration of the sweep kernel: threads per CTA (64, 128, 256, 384 or
  * 512; each CTA holds 32 replicas).  Results do not depend on it, only the
  * speed; the package's autotuner times the candidates and picks one.
  * PA_ERR_ARG for other values. */

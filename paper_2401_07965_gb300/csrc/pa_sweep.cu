@@ -131,10 +131,14 @@ struct SiteCmp {
     uint32_t cls[D];
 };
 
-template <int D, bool EA>
-__device__ __forceinline__ void site_prepare(SiteCmp<D>& c, const uint32_t* ms, const uint8_t* jb,
-                                             const Geo& geo, int k, int colour, uint32_t A2x,
-                                             uint32_t B1k, uint32_t vmask) {
+// the site of a half-sweep and its neighbours (periodic)
+struct Nbr {
+    int s, xp, xm, yp, ym, zp, zm;
+};
+
+// generic: the k-th site of the colour, any even L (x fastest)
+template <int D>
+__device__ __forceinline__ Nbr site_index(const Geo& geo, int k, int colour) {
     const int L = geo.L;
     const int LL = L * L;
     const int s0 = 2 * k;
@@ -147,31 +151,43 @@ __device__ __forceinline__ void site_prepare(SiteCmp<D>& c, const uint32_t* ms, 
         y = q1;
     }
     const int off = ((y + z) & 1) != colour;
-    const int s = s0 + off;
+    Nbr n;
+    n.s = s0 + off;
     x += off;
-    const int xp = (x == L - 1) ? s - (L - 1) : s + 1;
-    const int xm = (x == 0) ? s + (L - 1) : s - 1;
-    const int yp = (y == L - 1) ? s - (L - 1) * L : s + L;
-    const int ym = (y == 0) ? s + (L - 1) * L : s - L;
-    const uint32_t w = ms[s];
-    uint32_t P0 = w ^ ms[xp], P1 = w ^ ms[xm], P2 = w ^ ms[yp], P3 = w ^ ms[ym];
-    uint32_t P4 = 0, P5 = 0;
-    int zm = 0;
+    n.xp = (x == L - 1) ? n.s - (L - 1) : n.s + 1;
+    n.xm = (x == 0) ? n.s + (L - 1) : n.s - 1;
+    n.yp = (y == L - 1) ? n.s - (L - 1) * L : n.s + L;
+    n.ym = (y == 0) ? n.s + (L - 1) * L : n.s - L;
+    n.zp = n.zm = 0;
     if (D == 3) {
-        const int zp = (z == L - 1) ? s - (L - 1) * LL : s + LL;
-        zm = (z == 0) ? s + (L - 1) * LL : s - LL;
-        P4 = w ^ ms[zp];
-        P5 = w ^ ms[zm];
+        n.zp = (z == L - 1) ? n.s - (L - 1) * LL : n.s + LL;
+        n.zm = (z == 0) ? n.s + (L - 1) * LL : n.s - LL;
+    }
+    return n;
+}
+
+// classes of the site's replicas and the site-dependent Philox rounds 2 and 3
+template <int D, bool EA>
+__device__ __forceinline__ void site_prepare(SiteCmp<D>& c, const uint32_t* ms, const uint8_t* jb,
+                                             const Nbr& n, uint32_t A2x, uint32_t B1k,
+                                             uint32_t vmask) {
+    const int s = n.s;
+    const uint32_t w = ms[s];
+    uint32_t P0 = w ^ ms[n.xp], P1 = w ^ ms[n.xm], P2 = w ^ ms[n.yp], P3 = w ^ ms[n.ym];
+    uint32_t P4 = 0, P5 = 0;
+    if (D == 3) {
+        P4 = w ^ ms[n.zp];
+        P5 = w ^ ms[n.zm];
     }
     if (EA) {
         const uint32_t js = jb[s];
         P0 ^= 0u - (js & 1u);
-        P1 ^= 0u - (uint32_t)(jb[xm] & 1u);
+        P1 ^= 0u - (uint32_t)(jb[n.xm] & 1u);
         P2 ^= 0u - ((js >> 1) & 1u);
-        P3 ^= 0u - (uint32_t)((jb[ym] >> 1) & 1u);
+        P3 ^= 0u - (uint32_t)((jb[n.ym] >> 1) & 1u);
         if (D == 3) {
             P4 ^= 0u - ((js >> 2) & 1u);
-            P5 ^= 0u - (uint32_t)((jb[zm] >> 2) & 1u);
+            P5 ^= 0u - (uint32_t)((jb[n.zm] >> 2) & 1u);
         }
     }
     // classes of dE = 4 (d - n), n unsatisfied bonds
@@ -269,6 +285,35 @@ __device__ __forceinline__ void block_compare(SiteCmp<D>& c, const PlaneTab& e,
     c.lt = lt;
 }
 
+// planes 0-7 (blocks 0 and 1) at once: for each replica, u's top 8 bits
+// against thr's, by the borrow of the subtraction run from the least
+// significant plane up, b' = (~u & t) | (~(u ^ t) & b): b ends as [u8 < t8],
+// eq as [u8 == t8].  Replicas outside the classes see t = 0 and end with
+// b = 0.  Same result as the plane-by-plane comparison from the top.
+template <int D>
+__device__ __forceinline__ void compare8(SiteCmp<D>& c, const PlaneTab& e, const PlaneTab& f,
+                                         const uint32_t (&W)[4], const uint32_t (&V)[4]) {
+    uint32_t b = 0u, eq = 0xFFFFFFFFu;
+#pragma unroll
+    for (int m = 3; m >= 0; --m) {
+        uint32_t t = c.cls[0] & f.B[m][0];
+#pragma unroll
+        for (int a = 1; a < D; ++a) t |= c.cls[a] & f.B[m][a];
+        b = (~V[m] & t) | (~(V[m] ^ t) & b);
+        eq &= ~(V[m] ^ t);
+    }
+#pragma unroll
+    for (int m = 3; m >= 0; --m) {
+        uint32_t t = c.cls[0] & e.B[m][0];
+#pragma unroll
+        for (int a = 1; a < D; ++a) t |= c.cls[a] & e.B[m][a];
+        b = (~W[m] & t) | (~(W[m] ^ t) & b);
+        eq &= ~(W[m] ^ t);
+    }
+    c.lt = b & c.need;
+    c.und = eq & c.need;
+}
+
 template <int D>
 __device__ __forceinline__ void plane_block(SiteCmp<D>& c, const PlaneTab& e, const KParams& p) {
     uint32_t W[4];
@@ -313,10 +358,13 @@ struct SiteQueue {
     }
 };
 
-// sites queued per half-sweep: a quarter of the sites of a colour, at least 32
+// sites queued per half-sweep.  A site is still undecided after two plane
+// blocks (8 bits of u) with probability 1 - (1 - 2^-8)^32 = 11.8% at most, so
+// 5/32 of the sites of a colour plus 32 leaves the queue full only in rare
+// fluctuations (those sites finish inline); the small queue lets seven CTAs
+// of a 64 x 64 lattice share an SM.
 __host__ __device__ __forceinline__ int queue_capacity(int N) {
-    const int c = N / 8;
-    return c < 32 ? 32 : c;
+    return (((N / 2) * 5 / 32 + 32) + 31) / 32 * 32;
 }
 
 // ---------------------------------------------------------------------------
@@ -397,6 +445,10 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
         const uint32_t A2x = h0a ^ p.rk1[0];     // round-1 lane 2 without the site
         const uint32_t B1k = l1a ^ p.rk0[1];     // round-2 lane 0 key part
         const int nhalf = N / 2;
+        // row-wise walk of the sites (2D, L a power of two dividing the CTA size)
+        const int lgL = __ffs(geo.L) - 1;
+        const int rows2 = (D == 2 && (geo.L & (geo.L - 1)) == 0 && NT % geo.L == 0)
+                              ? 2 * NT / geo.L : 0;
         const uint32_t nh = 2u * theta;          // half-sweeps
         SiteQueue<D> queue;
         queue.w = qwords;
@@ -417,24 +469,45 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
             if (threadIdx.x == 0) qn[(h + 1) & 1u] = 0;
             const PlaneTab* tab = tabs[h & 1u];
             // pass 1: every site runs plane blocks 0 and 1 (decides ~88% of sites)
-            for (int k = threadIdx.x; k < nhalf; k += blockDim.x) {
+            auto pass1 = [&](const Nbr& n) {
                 SiteCmp<D> c;
-                site_prepare<D, EA>(c, ms, jb, geo, k, colour, A2x, B1k, vmask);
+                site_prepare<D, EA>(c, ms, jb, n, A2x, B1k, vmask);
                 if (c.need) {
                     uint32_t W[4], V[4];
                     block_draw2<D>(c, tab[0], tab[1], p, W, V);
-                    block_compare<D>(c, tab[0], W);
-                    block_compare<D>(c, tab[1], V);
+                    compare8<D>(c, tab[0], tab[1], W, V);
                 }
                 if (c.und) {
                     const int e = atomicAdd(&qn[h & 1u], 1);
                     if (e < qcap) {
                         queue.put(e, c);
-                        continue;
+                        return;
                     }
                     for (int g = 2; g < 8 && c.und; ++g) plane_block<D>(c, tab[g], p);
                 }
                 acc += site_flip<D>(c, ms, vmask);
+            };
+            if (rows2) {
+                // 2D, L = 2^lgL, 2 NT / L rows per pass (even): the thread's x is
+                // the same in every row it visits, and the row wrap is a mask
+                const int L = geo.L;
+                const int x = 2 * (int)(threadIdx.x & ((L >> 1) - 1)) +
+                              (((int)(threadIdx.x >> (lgL - 1)) + colour) & 1);
+                const int dxp = (x == L - 1) ? -(L - 1) : 1;
+                const int dxm = (x == 0) ? (L - 1) : -1;
+                for (int y = (int)(threadIdx.x >> (lgL - 1)); y < L; y += rows2) {
+                    Nbr n;
+                    n.s = (y << lgL) + x;
+                    n.xp = n.s + dxp;
+                    n.xm = n.s + dxm;
+                    n.yp = (n.s + L) & (N - 1);
+                    n.ym = (n.s - L) & (N - 1);
+                    n.zp = n.zm = 0;
+                    pass1(n);
+                }
+            } else {
+                for (int k = threadIdx.x; k < nhalf; k += blockDim.x)
+                    pass1(site_index<D>(geo, k, colour));
             }
             __syncthreads();
             // pass 2: the undecided sites, one per thread, from plane block 2 on
@@ -545,7 +618,9 @@ int sweep_threads(int N) {
     return t;
 }
 
-bool sweep_threads_supported(int t) { return t == 64 || t == 128 || t == 256 || t == 512; }
+bool sweep_threads_supported(int t) {
+    return t == 64 || t == 128 || t == 256 || t == 384 || t == 512;
+}
 
 static size_t group_smem(const KParams& p) {
     const size_t words_per_entry = 7 + (size_t)p.d;
@@ -579,6 +654,7 @@ static cudaError_t launch_group_t(const KParams& p, int mode, int threads, cudaS
     switch (threads) {
         case 64: return launch_group_nt<D, EA, 64>(p, mode, s);
         case 128: return launch_group_nt<D, EA, 128>(p, mode, s);
+        case 384: return launch_group_nt<D, EA, 384>(p, mode, s);
         case 512: return launch_group_nt<D, EA, 512>(p, mode, s);
         default: return launch_group_nt<D, EA, 256>(p, mode, s);
     }
@@ -596,6 +672,7 @@ static cudaError_t prepare_t(int threads) {
     switch (threads) {
         case 64: return prepare_nt<D, EA, 64>();
         case 128: return prepare_nt<D, EA, 128>();
+        case 384: return prepare_nt<D, EA, 384>();
         case 512: return prepare_nt<D, EA, 512>();
         default: return prepare_nt<D, EA, 256>();
     }

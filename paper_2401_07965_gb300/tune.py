@@ -17,7 +17,7 @@ import numpy as np
 
 from . import pa
 
-CANDIDATES = (64, 128, 256, 512)
+CANDIDATES = (64, 128, 256, 384, 512)
 _CACHE = {}
 _CACHE_FILE = os.path.join(os.path.expanduser("~"), ".cache", "pa_gb300_tune.json")
 
