@@ -291,6 +291,26 @@ pa_status pa_run_get_array(pa_ctx *ctx, int32_t run, pa_array which, void *host,
 pa_status pa_weighted(pa_ctx *ctx, int32_t ensemble, pa_weighted_obs *rows, int32_t max_rows,
                       int32_t *n_rows);
 
+
+/* Overlap distribution of two independent populations of one disorder sample
+ * (the spin-glass observable P(q) of Sec. 4, Figs. 6 and 7).  Pair p is
+ * (run_a[p], run_b[p]), two different runs of this batch with the same lattice
+ * and couplings (ideally different seeds, i.e. different run indices).  At the
+ * current step, replica slot j of run a is paired with slot j of run b for
+ * j < min(R_i^a, R_i^b); the pair's overlap is q = (1/N) sum_s s^a_s s^b_s =
+ * 1 - 2k/N with k the number of sites where the two differ.
+ *   hist_dev: device array of n_pairs x (N+1) uint32, caller-owned, row-major;
+ *             overwritten with the number of replica pairs at each k.
+ *   P_out:    host array of N+1 doubles, or NULL.  When given, receives the
+ *             weighted estimate P(k) = sum_p omega_p hist_p[k] / n_p with
+ *             omega_p proportional to (R_i^a Zhat_a)(R_i^b Zhat_b), the product
+ *             of the two populations' weights of Eq. (weighted-averages), and
+ *             the call synchronises; with NULL the histogram kernel is only
+ *             enqueued on the context's stream.
+ * All runs of the pairs must have the same N; 1 <= n_pairs <= batch size.
+ * PA_ERR_ARG otherwise. */
+pa_status pa_overlap(pa_ctx *ctx, const int32_t *run_a, const int32_t *run_b, int32_t n_pairs,
+                     uint32_t *hist_dev, double *P_out);
 /* Replay each temperature step as one captured CUDA graph (default on; needs a
  * non-NULL stream; timing mode launches directly). */
 pa_status pa_set_graph(pa_ctx *ctx, int32_t on);

@@ -8,12 +8,17 @@
 #include <new>
 #include <vector>
 
+#include <algorithm>
+
 #include "../../include/pa.h"
 #include "pa_internal.cuh"
 
 namespace pa {
 cudaError_t launch_weighted(const KParams& p, const int32_t* run_ids, int n_runs, int n_rows,
                             pa_weighted_obs* out, cudaStream_t s);
+cudaError_t launch_overlap(const KParams& p, const int32_t* pairs, int n_pairs, int Wp,
+                           uint32_t max_rows, int bins, uint32_t* hist, double* P,
+                           cudaStream_t s);
 }
 
 using namespace pa;
@@ -36,7 +41,7 @@ enum Region {
 
 enum Shared {
     S_RUNS, S_B2R, S_G2R, S_BETA, S_DBETA, S_Q, S_THR, S_THETA, S_IDS, S_WOUT,
-    S_CTL, S_GBETA, S_GTHR, S_GDB, S_GQ, S_COUNT
+    S_CTL, S_GBETA, S_GTHR, S_GDB, S_GQ, S_PAIRS, S_POV, S_COUNT
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -74,6 +79,8 @@ struct pa_ctx {
     std::vector<uint32_t> theta;
     int32_t* d_ids = nullptr;               // run index list for pa_weighted (device)
     pa_weighted_obs* d_wout = nullptr;      // its output rows (device)
+    int32_t* d_pairs = nullptr;             // run pairs for pa_overlap (device)
+    double* d_pov = nullptr;                // its weighted P(q) (device)
     bool controlled = false;                // learned schedule active
     bool finished = false;                  // beta_f reached under the controller
     CtlDev* d_ctl = nullptr;
@@ -158,6 +165,10 @@ Layout make_layout(const std::vector<RunHost>& runs, int n_steps) {
     sz[S_GBETA] = (size_t)(n_steps + 1) * 8;
     sz[S_GTHR] = (size_t)(n_steps + 1) * 16;
     sz[S_GDB] = sz[S_GQ] = (size_t)(n_steps + 1) * CTL_UMAX * 8;
+    int maxN = 0;
+    for (const RunHost& h : runs) maxN = h.N > maxN ? h.N : maxN;
+    sz[S_PAIRS] = M * 2 * 4;
+    sz[S_POV] = (size_t)(maxN + 1) * 8;
     size_t o = 0;
     for (int r = 0; r < S_COUNT; ++r) {
         L.shared_off[r] = o;
@@ -475,6 +486,8 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     p.theta = (const uint32_t*)(base + lay.shared_off[S_THETA]);
     ctx->d_ids = (int32_t*)(base + lay.shared_off[S_IDS]);
     ctx->d_wout = (pa_weighted_obs*)(base + lay.shared_off[S_WOUT]);
+    ctx->d_pairs = (int32_t*)(base + lay.shared_off[S_PAIRS]);
+    ctx->d_pov = (double*)(base + lay.shared_off[S_POV]);
     p.beta_rw = (double*)p.beta;
     p.dbeta_rw = (double*)p.dbeta;
     p.q_rw = (double*)p.q;
@@ -846,6 +859,34 @@ pa_status pa_weighted(pa_ctx* ctx, int32_t ensemble, pa_weighted_obs* rows, int3
                            cudaMemcpyDeviceToHost));
     }
     if (n_rows) *n_rows = n;
+    return PA_OK;
+}
+
+pa_status pa_overlap(pa_ctx* ctx, const int32_t* run_a, const int32_t* run_b, int32_t n_pairs,
+                     uint32_t* hist_dev, double* P_out) {
+    if (!ctx || !run_a || !run_b || !hist_dev || n_pairs < 1 || n_pairs > ctx->M)
+        return PA_ERR_ARG;
+    if (ctx->sticky != PA_OK) return PA_ERR_STATE;
+    std::vector<int32_t> pairs((size_t)2 * n_pairs);
+    uint32_t rows = 0;
+    const int N = valid_run(ctx, run_a[0]) ? ctx->runs[run_a[0]].N : -1;
+    for (int q = 0; q < n_pairs; ++q) {
+        const int a = run_a[q], b = run_b[q];
+        if (!valid_run(ctx, a) || !valid_run(ctx, b) || a == b) return PA_ERR_ARG;
+        if (ctx->runs[a].N != N || ctx->runs[b].N != N) return PA_ERR_ARG;
+        pairs[2 * q] = a;
+        pairs[2 * q + 1] = b;
+        rows = std::max(rows, std::min(ctx->runs[a].Rcap, ctx->runs[b].Rcap));
+    }
+    PA_CUDA(cudaMemcpyAsync(ctx->d_pairs, pairs.data(), pairs.size() * 4, cudaMemcpyHostToDevice,
+                            ctx->stream));
+    PA_CUDA(launch_overlap(ctx->kp, ctx->d_pairs, n_pairs, ctx->runs[run_a[0]].Wp, rows, N + 1,
+                           hist_dev, P_out ? ctx->d_pov : nullptr, ctx->stream));
+    ctx->launches += P_out ? 2 : 1;
+    if (!P_out) return PA_OK;  // asynchronous on the context's stream
+    pa_status st = pa_sync(ctx);
+    if (st != PA_OK) return st;
+    PA_CUDA(cudaMemcpy(P_out, ctx->d_pov, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost));
     return PA_OK;
 }
 

@@ -34,7 +34,7 @@ EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observable
            "pa_batch_workspace_bytes", "pa_batch_init", "pa_batch_size", "pa_run_observables",
            "pa_run_trace", "pa_run_free_energy", "pa_run_get_array", "pa_weighted",
            "pa_set_graph", "pa_set_controller", "pa_schedule_taken", "pa_mlp_scratch_bytes",
-           "pa_mlp_forward", "pa_mlp_gradients", "pa_mlp_adam"]
+           "pa_mlp_forward", "pa_mlp_gradients", "pa_mlp_adam", "pa_overlap"]
 
 
 class pa_lattice(C.Structure):
@@ -145,6 +145,8 @@ def _load():
     lib.pa_weighted.argtypes = [vp, C.c_int32, C.POINTER(pa_weighted_obs), C.c_int32,
                                 C.POINTER(C.c_int32)]
     lib.pa_set_graph.argtypes = [vp, C.c_int32]
+    lib.pa_overlap.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32,
+                               vp, C.POINTER(C.c_double)]
     lib.pa_set_controller.argtypes = [vp, C.POINTER(pa_controller)]
     lib.pa_schedule_taken.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint32),
                                       C.c_int32, C.POINTER(C.c_int32)]
@@ -375,6 +377,22 @@ def pa_set_graph(ctx, on=True):
     _check(_lib.pa_set_graph(ctx, 1 if on else 0), "pa_set_graph")
 
 
+def pa_overlap(ctx, run_a, run_b, hist_dev_ptr, N, weighted=True):
+    """Overlap histograms of run pairs into a device buffer (n_pairs x (N+1) uint32);
+    returns the weighted P(k) as a numpy array (or None with weighted=False: asynchronous)."""
+    a = np.ascontiguousarray(run_a, np.int32)
+    b = np.ascontiguousarray(run_b, np.int32)
+    if a.shape != b.shape:
+        raise ValueError("run_a and run_b differ in length")
+    P = np.zeros(int(N) + 1, np.float64) if weighted else None
+    _check(_lib.pa_overlap(ctx, a.ctypes.data_as(C.POINTER(C.c_int32)),
+                           b.ctypes.data_as(C.POINTER(C.c_int32)), int(a.size),
+                           C.c_void_p(hist_dev_ptr),
+                           P.ctypes.data_as(C.POINTER(C.c_double)) if weighted else None),
+           "pa_overlap")
+    return P
+
+
 def pa_set_controller(ctx, params_bf16, use_mlp, plain_units, plain_theta, theta_min,
                       theta_max, budget, u_max):
     bits = None if params_bf16 is None else np.ascontiguousarray(params_bf16, np.uint16)
@@ -578,6 +596,17 @@ class Batch:
 
     def weighted(self, ensemble):
         return pa_weighted(self.ctx, ensemble, self.n_steps + 1)
+
+    def overlap(self, pairs):
+        """Overlap distribution of run pairs [(a, b), ...] at the current step:
+        (hist[n_pairs][N+1] of the number of differing sites k, weighted P(k))."""
+        import torch
+        spec = self.specs[pairs[0][0]]
+        N = spec["L"] ** spec["dim"]
+        hist = torch.empty((len(pairs), N + 1), dtype=torch.int32, device="cuda")
+        P = pa_overlap(self.ctx, [a for a, _ in pairs], [b for _, b in pairs], hist.data_ptr(),
+                       N)
+        return hist.cpu().numpy().view(np.uint32), P
 
     def array(self, run, which):
         spec = self.specs[run]
