@@ -46,7 +46,9 @@ class Obs(C.Structure):
     _fields_ = [("R_i", C.c_uint32), ("lnQ", C.c_double), ("sum_lnQ", C.c_double),
                 ("sumE", C.c_int64), ("sumE2", C.c_int64), ("sumAbsM", C.c_int64),
                 ("sumM2", C.c_int64), ("sumC2", C.c_int64), ("entropy", C.c_double),
-                ("sv", C.c_double), ("accepts", C.c_uint64)]
+                ("sv", C.c_double), ("accepts", C.c_uint64), ("ess", C.c_double),
+                ("resampled", C.c_int32), ("wsum", C.c_double), ("wE", C.c_double),
+                ("wE2", C.c_double), ("wAM", C.c_double), ("wM2", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,11 +96,14 @@ def lib():
                              ("or_run_spins", C.c_void_p), ("or_run_energies", C.c_void_p),
                              ("or_run_families", C.c_void_p), ("or_run_counts", C.c_void_p),
                              ("or_run_fixed_weights", C.c_void_p),
-                             ("or_run_ancestors", C.c_void_p)]:
+                             ("or_run_ancestors", C.c_void_p),
+                             ("or_run_weights", C.c_void_p)]:
                 f = getattr(L, name)
                 f.argtypes = [C.c_void_p]
                 f.restype = rt
             L.or_run_obs.argtypes = [C.c_void_p, C.POINTER(Obs)]
+            L.or_run_set_partial.argtypes = [C.c_void_p, C.c_double]
+            L.or_run_set_partial.restype = C.c_int
             _lib = L
     return _lib
 
@@ -181,7 +186,8 @@ def resample(E, R, dbeta, method, seed, step, run_id=0):
 class Run:
     """A whole PA run of the oracle: Run(...).step() advances one temperature step."""
 
-    def __init__(self, d, L, J, R, betas, thetas, method, seed, R_cap=0, slot_base=0, run_id=0):
+    def __init__(self, d, L, J, R, betas, thetas, method, seed, R_cap=0, slot_base=0, run_id=0,
+                 alpha=None):
         self.d, self.L, self.N = d, L, L ** d
         self.J = np.ascontiguousarray(J, np.int8)
         self.betas = np.ascontiguousarray(betas, np.float64)
@@ -193,6 +199,9 @@ class Run:
         if not self._h:
             raise ValueError("oracle: invalid run arguments")
         self.R = R
+        if alpha is not None and lib().or_run_set_partial(self._h, float(alpha)) != 0:
+            raise ValueError("oracle: invalid partial-resampling threshold")
+        self.partial = alpha is not None
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -237,6 +246,12 @@ class Run:
 
     def ancestors(self):
         return self._arr("or_run_ancestors", C.c_uint32, self.size, np.uint32)
+
+    def weights(self):
+        """Per-replica weights under partial resampling (ones otherwise)."""
+        if not self.partial:
+            return np.ones(self.size)
+        return self._arr("or_run_weights", C.c_double, self.size, np.float64)
 
     def obs(self) -> dict:
         o = Obs()

@@ -323,58 +323,20 @@ static uint32_t find_box(const uint64_t *C, uint32_t n, uint64_t p)
 }
 
 /*
- * Resampling from beta_{i-1} to beta_i = beta_{i-1} + dbeta.  run_id enters
- * the resampling draws' counter (c1 = 2 << 28 | run_id << 8 | rule), so that
- * runs advanced together draw independent numbers; a lone run has run_id 0.
- * Inputs: E[0..Rprev) (energies at beta_{i-1}), nominal size R, method.
- * Outputs: counts[0..Rprev), f_rep[0..Rprev) (2^-40 fixed-point tau-hat),
- * *lnQ, *Rnew.  Returns a status code.
+ * Copy counts of the parents j < Rprev from their fixed-point expected copy
+ * numbers f_rep (tau-hat in 2^-40 units), by the chosen rule (Sec. 3).
+ * run_id enters the resampling draws' counter.  Returns a status code.
  */
-int or_resample(const int32_t *E, uint32_t Rprev, uint32_t R, double dbeta,
-                int method, uint64_t seed, uint32_t step, uint32_t run_id,
-                uint32_t *counts, uint64_t *f_rep, double *lnQ, uint64_t *Rnew)
+static int counts_from_f(const uint64_t *f_rep, uint32_t Rprev, uint32_t R, int method,
+                         uint64_t seed, uint32_t step, uint32_t run_id, uint32_t *counts,
+                         uint64_t *Rnew)
 {
     const uint32_t dom = DOM_RESAMPLE | (run_id << 8);
-    int32_t Emin = E[0], Emax = E[0];
-    uint32_t j, K, P, k, h;
-    uint64_t *nlev, *flev, *C, T = 0, total = 0;
-    double *t, S, q;
+    uint32_t j;
+    uint64_t *C = (uint64_t *)calloc(Rprev, sizeof(uint64_t)), T = 0, total = 0;
     uint32_t x[4];
     int status = OR_OK;
-
-    for (j = 1; j < Rprev; ++j) {
-        if (E[j] < Emin) Emin = E[j];
-        if (E[j] > Emax) Emax = E[j];
-    }
-    K = (uint32_t)((Emax - Emin) / 4) + 1;
-    P = 1;
-    while (P < K) P <<= 1;
-    nlev = (uint64_t *)calloc(K, sizeof(uint64_t));
-    flev = (uint64_t *)calloc(K, sizeof(uint64_t));
-    t = (double *)calloc(P, sizeof(double));
-    C = (uint64_t *)calloc(Rprev, sizeof(uint64_t));
-    for (j = 0; j < Rprev; ++j) nlev[(E[j] - Emin) / 4] += 1;
-
-    /* Boltzmann factor relative to the lowest energy: exp(-dbeta (E - Emin))
-     * = q^k for E = Emin + 4k. */
-    q = exp(-(4.0 * dbeta));
-    for (k = 0; k < K; ++k) t[k] = (double)nlev[k] * pow_bin(q, k);
-    /* S = sum_k n_k w_k in a fixed pairwise tree: t[k] += t[k + h] for
-     * h = P/2, P/4, ..., 1. */
-    for (h = P >> 1; h >= 1; h >>= 1)
-        for (k = 0; k < h; ++k) t[k] = t[k] + t[k + h];
-    S = t[0];
-    /* ln Q = ln( (1/R_{i-1}) sum_j exp(-dbeta E_j) ) */
-    *lnQ = (log(S) - log((double)Rprev)) - dbeta * (double)Emin;
-    /* tau-hat_k = R w_k / S in 2^-40 fixed point */
-    for (k = 0; k < K; ++k) {
-        double a = (double)R * pow_bin(q, k);
-        a = a / S;
-        a = ldexp(a, FRAC_BITS);
-        flev[k] = (uint64_t)floor(a);
-    }
     for (j = 0; j < Rprev; ++j) {
-        f_rep[j] = flev[(E[j] - Emin) / 4];
         T += f_rep[j];
         C[j] = T;
         counts[j] = 0;
@@ -467,7 +429,61 @@ int or_resample(const int32_t *E, uint32_t Rprev, uint32_t R, double dbeta,
     }
     for (j = 0; j < Rprev; ++j) total += counts[j];
     *Rnew = total;
-    free(nlev); free(flev); free(t); free(C);
+    free(C);
+    return status;
+}
+
+/*
+ * Resampling from beta_{i-1} to beta_i = beta_{i-1} + dbeta.  run_id enters
+ * the resampling draws' counter (c1 = 2 << 28 | run_id << 8 | rule), so that
+ * runs advanced together draw independent numbers; a lone run has run_id 0.
+ * Inputs: E[0..Rprev) (energies at beta_{i-1}), nominal size R, method.
+ * Outputs: counts[0..Rprev), f_rep[0..Rprev) (2^-40 fixed-point tau-hat),
+ * *lnQ, *Rnew.  Returns a status code.
+ */
+int or_resample(const int32_t *E, uint32_t Rprev, uint32_t R, double dbeta,
+                int method, uint64_t seed, uint32_t step, uint32_t run_id,
+                uint32_t *counts, uint64_t *f_rep, double *lnQ, uint64_t *Rnew)
+{
+    int32_t Emin = E[0], Emax = E[0];
+    uint32_t j, K, P, k, h;
+    uint64_t *nlev, *flev;
+    double *t, S, q;
+    int status;
+
+    for (j = 1; j < Rprev; ++j) {
+        if (E[j] < Emin) Emin = E[j];
+        if (E[j] > Emax) Emax = E[j];
+    }
+    K = (uint32_t)((Emax - Emin) / 4) + 1;
+    P = 1;
+    while (P < K) P <<= 1;
+    nlev = (uint64_t *)calloc(K, sizeof(uint64_t));
+    flev = (uint64_t *)calloc(K, sizeof(uint64_t));
+    t = (double *)calloc(P, sizeof(double));
+    for (j = 0; j < Rprev; ++j) nlev[(E[j] - Emin) / 4] += 1;
+
+    /* Boltzmann factor relative to the lowest energy: exp(-dbeta (E - Emin))
+     * = q^k for E = Emin + 4k. */
+    q = exp(-(4.0 * dbeta));
+    for (k = 0; k < K; ++k) t[k] = (double)nlev[k] * pow_bin(q, k);
+    /* S = sum_k n_k w_k in a fixed pairwise tree: t[k] += t[k + h] for
+     * h = P/2, P/4, ..., 1. */
+    for (h = P >> 1; h >= 1; h >>= 1)
+        for (k = 0; k < h; ++k) t[k] = t[k] + t[k + h];
+    S = t[0];
+    /* ln Q = ln( (1/R_{i-1}) sum_j exp(-dbeta E_j) ) */
+    *lnQ = (log(S) - log((double)Rprev)) - dbeta * (double)Emin;
+    /* tau-hat_k = R w_k / S in 2^-40 fixed point */
+    for (k = 0; k < K; ++k) {
+        double a = (double)R * pow_bin(q, k);
+        a = a / S;
+        a = ldexp(a, FRAC_BITS);
+        flev[k] = (uint64_t)floor(a);
+    }
+    for (j = 0; j < Rprev; ++j) f_rep[j] = flev[(E[j] - Emin) / 4];
+    status = counts_from_f(f_rep, Rprev, R, method, seed, step, run_id, counts, Rnew);
+    free(nlev); free(flev); free(t);
     return status;
 }
 
@@ -480,6 +496,11 @@ typedef struct {
     int64_t sumE, sumE2, sumAbsM, sumM2, sumC2;
     double entropy, sv;
     uint64_t accepts;
+    /* partial resampling: effective size of the reweighted population, whether
+     * the step resampled, and the weighted sums sum_j w_j O_j */
+    double ess;
+    int32_t resampled;
+    double wsum, wE, wE2, wAM, wM2;
 } or_obs;
 
 typedef struct {
@@ -504,7 +525,30 @@ typedef struct {
     double sum_lnQ;
     or_obs obs;
     int status;
+    /* partial resampling (alpha >= 0): per-replica weights w (double-buffered
+     * with the population); alpha < 0 resamples at every step */
+    double alpha;
+    double *w, *w2, *wn;
+    double ess;
+    int32_t resampled;
 } or_run;
+
+/* Sum of v[0..n) as the balanced binary tree over P = 2^ceil(log2 n) slots
+ * (slots past n hold 0): adjacent pairs are added, then adjacent pairs of
+ * those sums, and so on. */
+static double tree_sum(const double *v, uint32_t n)
+{
+    uint32_t P = 1, k, w;
+    double *t, s;
+    while (P < n) P <<= 1;
+    t = (double *)calloc(P, sizeof(double));
+    for (k = 0; k < n; ++k) t[k] = v[k];
+    for (w = 1; w < P; w <<= 1)
+        for (k = 0; k + w < P; k += 2 * w) t[k] = t[k] + t[k + w];
+    s = t[0];
+    free(t);
+    return s;
+}
 
 static void measure(or_run *r, const uint32_t *counts, const uint64_t *f_rep, uint32_t Rprev,
                     double lnQ, uint64_t acc)
@@ -545,8 +589,93 @@ static void measure(or_run *r, const uint32_t *counts, const uint64_t *f_rep, ui
         o.sv = s / (double)Rprev;
     }
     o.accepts = acc;
+    /* weighted sums over the population (all weights 1 without partial
+     * resampling) */
+    {
+        uint32_t n = r->Rcur;
+        double *v = (double *)calloc(n ? n : 1, sizeof(double));
+        const double *w = r->w;
+        o.ess = r->ess;
+        o.resampled = r->resampled;
+        for (j = 0; j < n; ++j) v[j] = w ? w[j] : 1.0;
+        o.wsum = tree_sum(v, n);
+        for (j = 0; j < n; ++j) v[j] = (w ? w[j] : 1.0) * (double)r->E[j];
+        o.wE = tree_sum(v, n);
+        for (j = 0; j < n; ++j)
+            v[j] = (w ? w[j] : 1.0) * ((double)r->E[j] * (double)r->E[j]);
+        o.wE2 = tree_sum(v, n);
+        for (j = 0; j < n; ++j) {
+            double M = (double)or_magnetisation(N, r->sig + (size_t)j * N);
+            v[j] = (w ? w[j] : 1.0) * (M < 0 ? -M : M);
+        }
+        o.wAM = tree_sum(v, n);
+        for (j = 0; j < n; ++j) {
+            double M = (double)or_magnetisation(N, r->sig + (size_t)j * N);
+            v[j] = (w ? w[j] : 1.0) * (M * M);
+        }
+        o.wM2 = tree_sum(v, n);
+        free(v);
+    }
     r->obs = o;
     free(fc);
+}
+
+/*
+ * Partial resampling (Sec. 3: resampling is needed only once the variance of
+ * the importance weights grows too large).  Replicas carry weights w_j; the
+ * step to beta_i multiplies them by the incremental weights
+ * gamma_j ~ exp(-dbeta (E_j - E_min)) = q^l_j (l_j = (E_j - E_min)/4,
+ * binary powering as for the level weights), giving wn_j, and
+ *   ln Q_i = ln(sum_j wn_j) - ln(sum_j w_j) - dbeta E_min,
+ *   ESS = (sum_j wn_j)^2 / sum_j wn_j^2   (sums: balanced binary trees).
+ * If ESS < alpha R_{i-1} the population is resampled with expected copy
+ * numbers R wn_j / sum wn (f_j = floor(2^40 R wn_j / S) as in the level
+ * form) and all weights restart at 1; otherwise every replica is kept once
+ * with its weight, rescaled by the power of two that puts the largest
+ * weight in [1/2, 1).
+ */
+static int partial_weights(or_run *r, uint32_t Rprev, double dbeta, uint32_t step,
+                           double *lnQ, uint64_t *Rnew, int *scale_exp)
+{
+    const int32_t *E = r->E;
+    int32_t Emin = E[0];
+    uint32_t j;
+    double q, S_old, S_new, S2, mx = 0.0;
+    double *sq = (double *)malloc(sizeof(double) * Rprev);
+    int status = OR_OK;
+    for (j = 1; j < Rprev; ++j)
+        if (E[j] < Emin) Emin = E[j];
+    q = exp(-(4.0 * dbeta));
+    for (j = 0; j < Rprev; ++j) {
+        r->wn[j] = r->w[j] * pow_bin(q, (uint32_t)((E[j] - Emin) / 4));
+        sq[j] = r->wn[j] * r->wn[j];
+        if (r->wn[j] > mx) mx = r->wn[j];
+    }
+    S_old = tree_sum(r->w, Rprev);
+    S_new = tree_sum(r->wn, Rprev);
+    S2 = tree_sum(sq, Rprev);
+    free(sq);
+    *lnQ = (log(S_new) - log(S_old)) - dbeta * (double)Emin;
+    r->ess = (S_new * S_new) / S2;
+    r->resampled = r->ess < r->alpha * (double)Rprev;
+    frexp(mx, scale_exp);
+    if (r->resampled) {
+        for (j = 0; j < Rprev; ++j) {
+            double a = (double)r->R * r->wn[j];
+            a = a / S_new;
+            a = ldexp(a, FRAC_BITS);
+            r->f_rep[j] = (uint64_t)floor(a);
+        }
+        status = counts_from_f(r->f_rep, Rprev, r->R, r->method, r->seed, step, r->run_id,
+                               r->counts, Rnew);
+    } else {
+        for (j = 0; j < Rprev; ++j) {
+            r->f_rep[j] = 1ull << FRAC_BITS;
+            r->counts[j] = 1u;
+        }
+        *Rnew = Rprev;
+    }
+    return status;
 }
 
 /* A run that is one of several advanced together: its replica slots are offset
@@ -596,8 +725,25 @@ or_run *or_run_create_ex(int d, int L, const int8_t *J, uint32_t R, uint32_t Rca
     r->Rprev = R;
     r->step = 0;
     r->sum_lnQ = 0.0;
+    r->alpha = -1.0;
     measure(r, NULL, NULL, 0, 0.0, 0);
     return r;
+}
+
+/* switch on partial resampling with threshold alpha in [0, 1] before the first
+ * step: all weights start at 1 */
+int or_run_set_partial(or_run *r, double alpha)
+{
+    uint32_t j;
+    if (!r || r->step != 0 || !(alpha >= 0.0 && alpha <= 1.0) || r->w) return OR_ERR_ARG;
+    r->alpha = alpha;
+    r->w = (double *)malloc(sizeof(double) * r->Rcap);
+    r->w2 = (double *)malloc(sizeof(double) * r->Rcap);
+    r->wn = (double *)malloc(sizeof(double) * r->Rcap);
+    for (j = 0; j < r->Rcap; ++j) r->w[j] = 1.0;
+    r->ess = (double)r->Rcur;
+    measure(r, NULL, NULL, 0, 0.0, 0);
+    return OR_OK;
 }
 
 or_run *or_run_create(int d, int L, const int8_t *J, uint32_t R, uint32_t Rcap, int n_steps,
@@ -612,6 +758,7 @@ void or_run_destroy(or_run *r)
     free(r->J); free(r->beta); free(r->theta);
     free(r->sig); free(r->sig2); free(r->E); free(r->E2);
     free(r->fam); free(r->fam2); free(r->counts); free(r->f_rep); free(r->anc);
+    free(r->w); free(r->w2); free(r->wn);
     free(r);
 }
 
@@ -621,6 +768,7 @@ int or_run_step(or_run *r)
     int i, N = r->N, st;
     uint32_t j, d, Rprev = r->Rcur;
     uint64_t Rnew = 0, acc = 0;
+    int scale_exp = 0;
     double dbeta, lnQ = 0.0;
     uint32_t thr[4];
     int8_t *ts;
@@ -630,9 +778,12 @@ int or_run_step(or_run *r)
     if (r->step >= r->n_steps) return OR_ERR_ARG;
     i = r->step + 1;
     dbeta = r->beta[i] - r->beta[i - 1];
-    /* step 2: resample */
-    st = or_resample(r->E, Rprev, r->R, dbeta, r->method, r->seed, (uint32_t)i, r->run_id,
-                     r->counts, r->f_rep, &lnQ, &Rnew);
+    /* step 2: resample (every step, or when the weights' ESS is too small) */
+    if (r->alpha >= 0.0)
+        st = partial_weights(r, Rprev, dbeta, (uint32_t)i, &lnQ, &Rnew, &scale_exp);
+    else
+        st = or_resample(r->E, Rprev, r->R, dbeta, r->method, r->seed, (uint32_t)i, r->run_id,
+                         r->counts, r->f_rep, &lnQ, &Rnew);
     if (st) { r->status = st; return st; }
     /* a population that outgrows its capacity, or dies out, stops the run */
     if (Rnew > r->Rcap || Rnew == 0) { r->status = OR_ERR_CAP; return OR_ERR_CAP; }
@@ -644,8 +795,12 @@ int or_run_step(or_run *r)
             memcpy(r->sig2 + (size_t)d * N, r->sig + (size_t)j * N, (size_t)N);
             r->E2[d] = r->E[j];
             r->fam2[d] = r->fam[j];
+            if (r->w) r->w2[d] = r->resampled ? 1.0 : ldexp(r->wn[j], -scale_exp);
             ++d;
         }
+    }
+    if (r->w) {
+        double *tw = r->w; r->w = r->w2; r->w2 = tw;
     }
     ts = r->sig; r->sig = r->sig2; r->sig2 = ts;
     te = r->E; r->E = r->E2; r->E2 = te;
@@ -677,5 +832,6 @@ const uint32_t *or_run_families(const or_run *r) { return r->fam; }
 const uint32_t *or_run_counts(const or_run *r) { return r->counts; }
 const uint64_t *or_run_fixed_weights(const or_run *r) { return r->f_rep; }
 const uint32_t *or_run_ancestors(const or_run *r) { return r->anc; }
+const double *or_run_weights(const or_run *r) { return r->w; }
 /* -beta F = ln Z_0 + sum ln Q, ln Z_0 = N ln 2 (Eq. free-energy-estimator) */
 double or_run_minus_beta_F(const or_run *r) { return (double)r->N * log(2.0) + r->sum_lnQ; }
