@@ -741,7 +741,9 @@ int or_run_set_partial(or_run *r, double alpha)
     r->w2 = (double *)malloc(sizeof(double) * r->Rcap);
     r->wn = (double *)malloc(sizeof(double) * r->Rcap);
     for (j = 0; j < r->Rcap; ++j) r->w[j] = 1.0;
+    /* the initial population is unweighted, as after a resampling */
     r->ess = (double)r->Rcur;
+    r->resampled = 1;
     measure(r, NULL, NULL, 0, 0.0, 0);
     return OR_OK;
 }
