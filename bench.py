@@ -694,6 +694,45 @@ def run_overlap(args):
     return 0
 
 
+def run_partial(args):
+    """Partial resampling (resample only when the effective size of the reweighted
+    population falls below alpha R) against resampling at every step: 2D Ising L=64,
+    R=10000, beta 0 -> 1 in 200 steps, theta=10, systematic, 5 seeds per arm; device time
+    per run (graph replay), resampling steps, free-energy error against Kaufman's value."""
+    import torch
+    from paper_2401_07965_gb300 import pa
+    L, R, n = 64, 10000, 200
+    betas = np.linspace(0.0, 1.0, n + 1)
+    thetas = np.full(n, 10, np.uint32)
+    exact = _kaufman(L, 1.0)
+    stream = torch.cuda.Stream()
+    arms = {}
+    for alpha in (None, 0.9, 0.5, 0.2):
+        ms, errs, res = [], [], []
+        for seed in (21, 22, 23, 24, 25):
+            b = pa.Batch([{"dim": 2, "L": L, "R": R}], betas, thetas, "systematic", seed,
+                         stream=stream)
+            if alpha is not None:
+                b.set_partial_resampling(alpha)
+            ms.append(_timed_batch(pa, b, n, stream))
+            mbf, _ = b.free_energy(0)
+            errs.append((mbf - exact) / (L * L))
+            res.append(sum(r["resampled"] for r in b.trace(0)[1:]))
+            b.close()
+        arms["every step" if alpha is None else f"alpha={alpha}"] = {
+            "ms": float(np.mean(ms)), "rms_f_err_per_spin": float(np.sqrt(np.mean(np.square(errs)))),
+            "max_f_err_per_spin": float(np.max(np.abs(errs))),
+            "resampling_steps": float(np.mean(res))}
+    base = arms["every step"]
+    _line("partial resampling: 2D Ising L=64, R=10000, beta 0->1 in 200 steps, theta=10, "
+          "systematic, 5 seeds; alpha = 0.9 / 0.5 / 0.2 against every step",
+          10.0 * L * L * R * n / (arms["alpha=0.5"]["ms"] * 1e6), arms["alpha=0.5"]["ms"], n, 0,
+          {"what": "spin updates/ns of a whole run with alpha = 0.5 (graph replay)",
+           "every_step_updates_per_ns": 10.0 * L * L * R * n / (base["ms"] * 1e6),
+           "arms": arms})
+    return 0
+
+
 def run_e2e(args, pa, stream, seed, dev, threads=0):
     """Whole runs through the C ABI: host schedule -> pa_init -> per step pa_step +
     pa_observables (device -> host) -> pa_free_energy.  Host wall clock."""
@@ -747,11 +786,12 @@ def main():
                     help="small: one run of R=20000 replicas of the same lattice (profiling)")
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "ea3d", "weighted", "accuracy", "controller",
-                             "overlap"],
+                             "overlap", "partial"],
                     help="headline: the benchmark line; ea3d / weighted: the batched "
                          "workloads; accuracy: time to a free energy within 1e-4 per spin; "
                          "controller: learned against plain schedule; overlap: P(q) of "
-                         "two populations per spin-glass sample")
+                         "two populations per spin-glass sample; partial: resampling only "
+                         "when the weights' effective size is low")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -769,6 +809,8 @@ def main():
         return run_controller(args)
     if args.workload == "overlap":
         return run_overlap(args)
+    if args.workload == "partial":
+        return run_partial(args)
     return run_ours(args)
 
 

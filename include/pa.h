@@ -96,7 +96,9 @@ typedef struct {
 } pa_schedule;
 
 /* Population averages after the sweeps of the current step (Sec. 2 step 4).
- * Integer sums are exact; e = <E>/N, m = M/N. */
+ * Integer sums are exact; e = <E>/N, m = M/N.  Under partial resampling
+ * (pa_set_partial_resampling) e, e2, absm, m2, c and chi are the weighted
+ * averages sum_j w_j O_j / sum_j w_j; the integer sums stay unweighted. */
 typedef struct {
     int32_t step;          /* completed temperature steps i                         */
     uint32_t R_i;          /* population size after step i                         */
@@ -118,6 +120,10 @@ typedef struct {
     float features[8];     /* learned schedule: the controller's inputs after step i */
     int32_t u_next;        /* its choice for step i+1: grid points (0 = none) ...   */
     uint32_t theta_next;   /* ... and sweeps                                        */
+    double ess;            /* partial resampling: (sum w)^2 / sum w^2 of the step's  */
+                           /* reweighted population (R_i otherwise)                 */
+    int32_t resampled;     /* partial resampling: 1 if step i resampled (always 1   */
+    int32_t pad1;          /* otherwise)                                             */
 } pa_obs;
 
 /* One run of a batch (pa_batch_init).  All runs of a batch share the
@@ -158,7 +164,9 @@ typedef enum {
     PA_ARRAY_FAMILY = 2,     /* uint32 [R_i] index of the initial ancestor         */
     PA_ARRAY_COUNTS = 3,     /* uint32 [R_prev] copy numbers r_j of the last step  */
     PA_ARRAY_ANCESTOR = 4,   /* uint32 [R_i] parent slot j of each new slot        */
-    PA_ARRAY_MAGNET = 5      /* int32  [R_i] magnetisation M = sum sigma           */
+    PA_ARRAY_MAGNET = 5,     /* int32  [R_i] magnetisation M = sum sigma           */
+    PA_ARRAY_WEIGHT = 6      /* double [R_i] replica weights (partial resampling;  */
+                             /*        1 otherwise)                                */
 } pa_array;
 
 /* Bytes of device workspace a context needs (0 on invalid arguments).
@@ -291,6 +299,22 @@ pa_status pa_run_get_array(pa_ctx *ctx, int32_t run, pa_array which, void *host,
 pa_status pa_weighted(pa_ctx *ctx, int32_t ensemble, pa_weighted_obs *rows, int32_t max_rows,
                       int32_t *n_rows);
 
+
+/* Partial resampling (Sec. 3: resampling is needed only once the variance of
+ * the importance weights grows too large).  Call after init, before the first
+ * step.  Replicas then carry weights w_j (initially 1).  Each step multiplies
+ * them by exp(-dbeta (E_j - E_min)) (the same q^l level factors), sets
+ *   ln Q_i = ln(sum_j wn_j) - ln(sum_j w_j) - dbeta E_min
+ * and resamples (expected copies R wn_j / sum wn, the context's rule) only if
+ * the effective size (sum wn)^2 / sum wn^2 is below alpha R_{i-1}; otherwise
+ * every replica is kept with its weight (rescaled by a power of two so the
+ * largest is in [1/2, 1)).  Sums are balanced binary trees over the replica
+ * index in FP64, so counts and decisions are reproducible.  alpha in [0, 1]:
+ * 0 never resamples (annealed importance sampling), 1 resamples whenever the
+ * weights differ.  Observables become weighted averages (pa_obs).  Every run
+ * of the batch needs R_cap <= 4096 x 2048; pa_set_state is then unavailable.
+ * PA_ERR_ARG for bad arguments or a context that has stepped. */
+pa_status pa_set_partial_resampling(pa_ctx *ctx, double alpha);
 
 /* Overlap distribution of two independent populations of one disorder sample
  * (the spin-glass observable P(q) of Sec. 4, Figs. 6 and 7).  Pair p is

@@ -36,7 +36,7 @@ struct RunHost {
 
 enum Region {
     R_SPIN0, R_SPIN1, R_E0, R_E1, R_F0, R_F1, R_M, R_ANC, R_CNT, R_C, R_G, R_HIST, R_FLEV, R_TREE,
-    R_PA, R_PB, R_OA, R_OB, R_PD, R_PCL, R_JB, R_ST, R_TRACE, R_COUNT
+    R_PA, R_PB, R_OA, R_OB, R_PD, R_PCL, R_W, R_WP, R_OP, R_JB, R_ST, R_TRACE, R_COUNT
 };
 
 enum Shared {
@@ -185,6 +185,9 @@ Layout make_layout(const std::vector<RunHost>& runs, int n_steps) {
         rs[R_FLEV] = (size_t)h.nlev * 8;
         rs[R_TREE] = (size_t)h.P * 8;
         rs[R_PA] = rs[R_PB] = rs[R_OA] = rs[R_OB] = rs[R_PD] = rs[R_PCL] = (size_t)h.nblk * 8;
+        rs[R_W] = rows * 8;
+        rs[R_WP] = (size_t)h.nblk * 4 * 8;
+        rs[R_OP] = (size_t)h.nblk * 5 * 8;
         rs[R_JB] = (size_t)h.N;
         rs[R_ST] = sizeof(DevState);
         rs[R_TRACE] = (size_t)(n_steps + 1) * sizeof(TraceRow);
@@ -297,10 +300,22 @@ void fill_obs(const pa_ctx* ctx, int run, const TraceRow& t, int step, pa_obs* o
     const double R = t.R_i ? (double)t.R_i : 1.0;
     o->entropy = std::log(R) - t.c_ln_c / R;
     o->sv = (step > 0 && t.R_prev) ? t.sv_sum / (double)t.R_prev : 0.0;
-    o->e = (double)o->sumE / (R * N);
-    o->e2 = (double)o->sumE2 / (R * N * N);
-    o->absm = (double)o->sumAbsM / (R * N);
-    o->m2 = (double)o->sumM2 / (R * N * N);
+    if (ctx->kp.alpha >= 0.0 && t.wsum > 0.0) {
+        // partial resampling: weighted averages
+        o->e = t.wE / (t.wsum * N);
+        o->e2 = t.wE2 / (t.wsum * N * N);
+        o->absm = t.wAM / (t.wsum * N);
+        o->m2 = t.wM2 / (t.wsum * N * N);
+        o->ess = t.ess;
+        o->resampled = t.resampled;
+    } else {
+        o->e = (double)o->sumE / (R * N);
+        o->e2 = (double)o->sumE2 / (R * N * N);
+        o->absm = (double)o->sumAbsM / (R * N);
+        o->m2 = (double)o->sumM2 / (R * N * N);
+        o->ess = (double)t.R_i;
+        o->resampled = 1;
+    }
     o->c = o->beta * o->beta * N * (o->e2 - o->e * o->e);
     o->chi = o->beta * N * (o->m2 - o->absm * o->absm);
     o->rho_t = (double)o->sumC2 / R;
@@ -494,6 +509,7 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     p.thr_rw = (uint32_t*)p.thr;
     p.theta_rw = (uint32_t*)p.theta;
     p.ctl = nullptr;
+    p.alpha = -1.0;
     ctx->d_ctl = (CtlDev*)(base + lay.shared_off[S_CTL]);
     ctx->d_gbeta = (double*)(base + lay.shared_off[S_GBETA]);
     ctx->d_gthr = (uint32_t*)(base + lay.shared_off[S_GTHR]);
@@ -549,6 +565,9 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
         r.offB = (uint64_t*)(base + off[R_OB]);
         r.partD = (double*)(base + off[R_PD]);
         r.partCL = (double*)(base + off[R_PCL]);
+        r.w = (double*)(base + off[R_W]);
+        r.wpart = (double*)(base + off[R_WP]);
+        r.opart = (double*)(base + off[R_OP]);
         r.jbits = (const uint8_t*)(base + off[R_JB]);
         r.st = (DevState*)(base + off[R_ST]);
         r.trace = (TraceRow*)(base + off[R_TRACE]);
@@ -786,6 +805,15 @@ pa_status pa_run_get_array(pa_ctx* ctx, int32_t run, pa_array which, void* host,
             if (capacity < n) return PA_ERR_ARG;
             if (n) PA_CUDA(cudaMemcpy(host, r.counts, n * 4, cudaMemcpyDeviceToHost));
             break;
+        case PA_ARRAY_WEIGHT:
+            n = st.R_cur;
+            if (capacity < n) return PA_ERR_ARG;
+            if (ctx->kp.alpha >= 0.0) {
+                if (n) PA_CUDA(cudaMemcpy(host, r.w, n * 8, cudaMemcpyDeviceToHost));
+            } else {
+                for (size_t j = 0; j < n; ++j) ((double*)host)[j] = 1.0;
+            }
+            break;
         default:
             return PA_ERR_ARG;
     }
@@ -800,7 +828,7 @@ pa_status pa_get_array(pa_ctx* ctx, pa_array which, void* host, size_t capacity,
 pa_status pa_set_state(pa_ctx* ctx, const uint32_t* spins, const uint32_t* family, uint32_t R_i,
                        int32_t step, double sum_lnQ) {
     if (!ctx || ctx->M != 1 || !spins || R_i == 0 || R_i > ctx->runs[0].Rcap || step < 0 ||
-        step > ctx->n_steps)
+        step > ctx->n_steps || ctx->kp.alpha >= 0.0)
         return PA_ERR_ARG;
     if (ctx->sticky != PA_OK) return PA_ERR_STATE;
     const RunDesc& r = ctx->desc[0];
@@ -888,6 +916,36 @@ pa_status pa_overlap(pa_ctx* ctx, const int32_t* run_a, const int32_t* run_b, in
     if (st != PA_OK) return st;
     PA_CUDA(cudaMemcpy(P_out, ctx->d_pov, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost));
     return PA_OK;
+}
+
+pa_status pa_set_partial_resampling(pa_ctx* ctx, double alpha) {
+    if (!ctx || ctx->host_step != 0 || ctx->kp.alpha >= 0.0 || !(alpha >= 0.0 && alpha <= 1.0))
+        return PA_ERR_ARG;
+    if (ctx->sticky != PA_OK) return PA_ERR_STATE;
+    for (const RunHost& h : ctx->runs)
+        if (h.nblk > PARTIAL_MAX_BLOCKS) return PA_ERR_ARG;
+    PA_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->kp.alpha = alpha;
+    PA_CUDA(launch_partial_init(ctx->kp, ctx->stream));
+    ctx->launches += 1;
+    // row 0: all weights are 1, so the weighted sums are the exact sums
+    for (int m = 0; m < ctx->M; ++m) {
+        TraceRow t;
+        PA_CUDA(cudaMemcpy(&t, ctx->desc[m].trace, sizeof(t), cudaMemcpyDeviceToHost));
+        t.ess = (double)t.R_i;
+        t.resampled = 1;
+        t.wsum = (double)t.R_i;
+        t.wE = (double)(long long)t.sumE;
+        t.wE2 = (double)(long long)t.sumE2;
+        t.wAM = (double)(long long)t.sumAbsM;
+        t.wM2 = (double)(long long)t.sumM2;
+        PA_CUDA(cudaMemcpy(ctx->desc[m].trace, &t, sizeof(t), cudaMemcpyHostToDevice));
+    }
+    if (ctx->graph) {  // the step graph must now include the weight kernels
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return pa_sync(ctx);
 }
 
 pa_status pa_set_controller(pa_ctx* ctx, const pa_controller* cfg) {

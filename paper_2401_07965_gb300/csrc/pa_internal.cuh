@@ -108,7 +108,9 @@ struct DevState {
     uint64_t Rres;     // residual draws
     int32_t kgrid;     // learned schedule: grid index of the current beta
     uint32_t sweeps;   // learned schedule: sweeps spent so far
-    uint64_t pad;
+    int32_t resample;  // partial resampling: this step resamples
+    int32_t wexp;      // partial resampling: exponent of the largest new weight
+    double S_new;      // partial resampling: sum of the new weights
 };
 
 // Per-step accumulators, device-resident (row i = after temperature step i).
@@ -122,6 +124,11 @@ struct TraceRow {
     float x[8];       // learned schedule: features seen by the controller after this step
     int32_t u_next;   // its choice: grid units of the next step (0 = none)
     uint32_t theta_next;  // and the sweeps of the next step
+    // partial resampling: effective size of the reweighted population, whether
+    // the step resampled, and the weighted sums sum_j w_j O_j after the sweeps
+    double ess;
+    int32_t resampled, pad;
+    double wsum, wE, wE2, wAM, wM2;
 };
 
 // Per-run description, in device memory (one per run of the batch).
@@ -152,6 +159,9 @@ struct RunDesc {
     uint64_t* offB;
     double* partD;
     double* partCL;
+    double* w;               // partial resampling: replica weights
+    double* wpart;           // per-block tree sums of the weights (4 per block)
+    double* opart;           // per-block tree sums of the weighted observables (5 per block)
     const uint8_t* jbits;    // bit a of byte s: bond (s, s+e_a) has J = -1
     DevState* st;
     TraceRow* trace;         // n_steps + 1 rows
@@ -179,7 +189,11 @@ struct KParams {
     uint32_t* thr_rw;
     uint32_t* theta_rw;
     const CtlDev* ctl;       // null without a controller
+    double alpha;            // partial resampling threshold (< 0: resample every step)
 };
+
+// partial resampling: blocks of a run whose tree sums one CTA can finish
+constexpr int PARTIAL_MAX_BLOCKS = 4096;
 
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
@@ -192,6 +206,7 @@ namespace pa {
 cudaError_t launch_init_spins(const KParams& p, const RunDesc* host_runs, cudaStream_t s);
 cudaError_t launch_measure(const KParams& p, int threads, cudaStream_t s);
 cudaError_t launch_resample(const KParams& p, cudaStream_t s, int64_t* launches);
+cudaError_t launch_partial_init(const KParams& p, cudaStream_t s);
 cudaError_t launch_sweep(const KParams& p, int threads, cudaStream_t s);
 cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int64_t* launches);
 cudaError_t prepare_sweep(const KParams& p, int threads);

@@ -11,6 +11,14 @@
 //   ln Q = (ln S - ln R_{i-1}) - dbeta E_min,
 //   f_k = floor(2^40 * ((R w_k) / S))  (tau-hat of Eq. taus in 2^-40 units).
 // The copy counts are exact integer functions of f and of Philox draws.
+//
+// Partial resampling (alpha >= 0): replicas carry weights w_j.  The step
+// multiplies them by the level factors q^(l_j - l_min) (k_pw_update), sums
+// old and new weights and the squares in balanced binary trees over the
+// replica index (blocks of SCAN_CHUNK aligned replicas, then the blocks:
+// k_pw_final), and resamples with f_j = floor(2^40 (R wn_j) / S_new) only if
+// (sum wn)^2 / sum wn^2 < alpha R_{i-1}; otherwise every replica is kept once
+// and its weight is rescaled by a power of two (k_family).
 #include <climits>
 
 #include "pa_internal.cuh"
@@ -106,6 +114,40 @@ __device__ __forceinline__ T block_excl_scan(T v, T* sh, T* total) {
     return res;
 }
 
+// balanced binary tree sums (adjacent pairs first) in explicitly rounded FP64:
+// over 8 or 16 consecutive values, and over the threads of a CTA (thread t =
+// leaf t, blockDim a power of two); the root ends in every thread
+__device__ __forceinline__ double tree8(const double* a) {
+    return __dadd_rn(__dadd_rn(__dadd_rn(a[0], a[1]), __dadd_rn(a[2], a[3])),
+                     __dadd_rn(__dadd_rn(a[4], a[5]), __dadd_rn(a[6], a[7])));
+}
+
+__device__ double tree_threads(double v, double* sh) {
+    const int t = threadIdx.x, n = blockDim.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int w = 1; w < n; w <<= 1) {
+        if ((t & (2 * w - 1)) == 0) sh[t] = __dadd_rn(sh[t], sh[t + w]);
+        __syncthreads();
+    }
+    const double root = sh[0];
+    __syncthreads();
+    return root;
+}
+
+__device__ double max_threads(double v, double* sh) {
+    const int t = threadIdx.x, n = blockDim.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int w = n >> 1; w >= 1; w >>= 1) {
+        if (t < w) sh[t] = fmax(sh[t], sh[t + w]);
+        __syncthreads();
+    }
+    const double root = sh[0];
+    __syncthreads();
+    return root;
+}
+
 // --------------------------------------------------------------------------
 // K3: weights, S, ln Q, f table (one CTA)
 // --------------------------------------------------------------------------
@@ -143,6 +185,25 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
     int P = 1;
     while (P < K) P <<= 1;
     const double q = p.q[i - 1];
+    if (p.alpha >= 0.0) {
+        // partial resampling: the level factors q^k; k_pw_final closes the step
+        double* wl = reinterpret_cast<double*>(r.flev);
+        for (int k = threadIdx.x; k < K; k += blockDim.x) wl[k] = pow_bin(q, (uint32_t)k);
+        __syncthreads();
+        for (int k = threadIdx.x; k < K; k += blockDim.x) r.hist[lmin + k] = 0u;
+        if (threadIdx.x == 0) {
+            st->R_prev = Rprev;
+            st->lmin = (uint32_t)lmin;
+            st->K = (uint32_t)K;
+            TraceRow* tr = r.trace + i;
+            tr->c_ln_c = 0.0;
+            tr->sv_sum = 0.0;
+            tr->sumE = tr->sumE2 = tr->sumAbsM = tr->sumM2 = tr->sumC2 = tr->accepts = 0ull;
+            tr->R_prev = Rprev;
+            tr->R_i = 0;
+        }
+        return;
+    }
     volatile double* t = r.tree;
     for (int k = threadIdx.x; k < P; k += blockDim.x)
         t[k] = (k < K) ? __dmul_rn((double)r.hist[lmin + k], pow_bin(q, (uint32_t)k)) : 0.0;
@@ -184,10 +245,111 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
 }
 
 // --------------------------------------------------------------------------
+// partial resampling: new weights and their per-block tree sums
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(SCAN_THREADS) k_pw_update(KParams p) {
+    const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
+    const uint32_t b = blockIdx.x - r.blk0;
+    const DevState* st = r.st;
+    if (st->status != S_OK) return;
+    __shared__ double sh[SCAN_THREADS];
+    const int i = st->step + 1;
+    const int32_t* E = r.E[(i - 1) & 1];
+    const uint32_t Rprev = st->R_prev, lmin = st->lmin;
+    const int dN = p.d * r.N;
+    const double* wl = reinterpret_cast<const double*>(r.flev);
+    const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    double wo[SCAN_ITEMS], wn[SCAN_ITEMS], w2[SCAN_ITEMS];
+    double mx = 0.0;
+#pragma unroll
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const int j = j0 + e;
+        wo[e] = wn[e] = w2[e] = 0.0;
+        if ((uint32_t)j < Rprev) {
+            wo[e] = r.w[j];
+            wn[e] = __dmul_rn(wo[e], wl[level_of(E[j], dN) - (int)lmin]);
+            w2[e] = __dmul_rn(wn[e], wn[e]);
+            r.w[j] = wn[e];
+            mx = fmax(mx, wn[e]);
+        }
+    }
+    const double s_old = tree_threads(tree8(wo), sh);
+    const double s_new = tree_threads(tree8(wn), sh);
+    const double s2 = tree_threads(tree8(w2), sh);
+    mx = max_threads(mx, sh);
+    if (threadIdx.x == 0) {
+        r.wpart[4 * b + 0] = s_old;
+        r.wpart[4 * b + 1] = s_new;
+        r.wpart[4 * b + 2] = s2;
+        r.wpart[4 * b + 3] = mx;
+    }
+}
+
+// one CTA per run: tree over the blocks, ln Q, effective size, decision
+__global__ void __launch_bounds__(1024) k_pw_final(KParams p) {
+    const RunDesc& r = p.runs[blockIdx.x];
+    DevState* st = r.st;
+    if (st->status != S_OK) return;
+    __shared__ double sh[1024];
+    const int i = st->step + 1;
+    const int nb = r.nblk;  // <= PARTIAL_MAX_BLOCKS = 4 leaves x 1024 threads
+    double S[3];
+    for (int q = 0; q < 3; ++q) {
+        double x[4];
+        for (int k = 0; k < 4; ++k) {
+            const int bb = 4 * threadIdx.x + k;
+            x[k] = bb < nb ? r.wpart[4 * bb + q] : 0.0;
+        }
+        S[q] = tree_threads(__dadd_rn(__dadd_rn(x[0], x[1]), __dadd_rn(x[2], x[3])), sh);
+    }
+    double mx = 0.0;
+    for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) mx = fmax(mx, r.wpart[4 * bb + 3]);
+    mx = max_threads(mx, sh);
+    if (threadIdx.x == 0) {
+        const uint32_t Rprev = st->R_prev;
+        const int32_t Umin = 2 * (int32_t)st->lmin + r.parity;
+        const int32_t Emin = 2 * Umin - p.d * r.N;
+        const double lnQ = __dsub_rn(__dsub_rn(log(S[1]), log(S[0])),
+                                     __dmul_rn(p.dbeta[i - 1], (double)Emin));
+        const double ess = __ddiv_rn(__dmul_rn(S[1], S[1]), S[2]);
+        const int res = ess < __dmul_rn(p.alpha, (double)Rprev) ? 1 : 0;
+        int e = 0;
+        frexp(mx, &e);
+        st->resample = res;
+        st->wexp = e;
+        st->S_new = S[1];
+        st->sum_lnQ = __dadd_rn(st->sum_lnQ, lnQ);
+        TraceRow* tr = r.trace + i;
+        tr->lnQ = lnQ;
+        tr->sum_lnQ = st->sum_lnQ;
+        tr->ess = ess;
+        tr->resampled = res;
+    }
+}
+
+// weights of a new run: 1
+__global__ void k_pw_init(KParams p) {
+    const RunDesc& r = p.runs[blockIdx.y];
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < r.Rcap; j += gridDim.x * blockDim.x)
+        r.w[j] = 1.0;
+}
+
+// --------------------------------------------------------------------------
 // per-block sums of f (and of its 2^-40 fractional part)
 // --------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t f_of(int j, const RunDesc& r, int dN, const int32_t* E,
+// expected copies of parent j in 2^-40 units: the level table, or under
+// partial resampling floor(2^40 (R wn_j) / S_new) when the step resamples and
+// exactly one copy when it does not
+__device__ __forceinline__ uint64_t f_of(int j, const KParams& p, const RunDesc& r,
+                                         const DevState* st, int dN, const int32_t* E,
                                          uint32_t lmin) {
+    if (p.alpha >= 0.0) {
+        if (!st->resample) return 1ull << FRAC_BITS;
+        double a = __dmul_rn((double)r.R, r.w[j]);
+        a = __ddiv_rn(a, st->S_new);
+        a = scalbn(a, FRAC_BITS);
+        return (uint64_t)floor(a);
+    }
     return r.flev[level_of(E[j], dN) - (int)lmin];
 }
 
@@ -206,7 +368,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_fsum(KParams p) {
     for (int e = 0; e < SCAN_ITEMS; ++e) {
         const int j = j0 + e;
         if ((uint32_t)j < Rprev) {
-            const uint64_t f = f_of(j, r, dN, E, lmin);
+            const uint64_t f = f_of(j, p, r, st, dN, E, lmin);
             sf += f;
             sg += f & ((1ull << FRAC_BITS) - 1);
         }
@@ -282,7 +444,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_counts(KParams p) {
 #pragma unroll
     for (int e = 0; e < SCAN_ITEMS; ++e) {
         const int j = j0 + e;
-        f[e] = ((uint32_t)j < Rprev) ? f_of(j, r, dN, E, lmin) : 0ull;
+        f[e] = ((uint32_t)j < Rprev) ? f_of(j, p, r, st, dN, E, lmin) : 0ull;
         sf += f[e];
         sg += f[e] & ((1ull << FRAC_BITS) - 1);
     }
@@ -294,6 +456,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_counts(KParams p) {
     if (method == M_SYSTEMATIC)
         usys = philox(0u, DOM_RESAMPLE | (r.run << 8) | RULE_SYSTEMATIC, (uint32_t)i, 0u, p.k0, p.k1).x;
     bool kmax = false;
+    const bool keep = p.alpha >= 0.0 && !st->resample;  // partial: every replica once
 #pragma unroll 1
     for (int e = 0; e < SCAN_ITEMS; ++e) {
         const int j = j0 + e;
@@ -304,7 +467,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_counts(KParams p) {
         r.C[j] = cf;
         if (method == M_RESIDUAL) r.G[j] = cg;
         uint32_t cnt = 0;
-        if (method == M_NEAREST) {
+        if (keep) {
+            cnt = 1u;
+        } else if (method == M_NEAREST) {
             const uint4x x = philox((uint32_t)j, DOM_RESAMPLE | (r.run << 8) | RULE_NEAREST, (uint32_t)i, 0u,
                                     p.k0, p.k1);
             const uint64_t u40 = (((uint64_t)x.y << 32) | x.x) >> 24;
@@ -351,6 +516,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_draws(KParams p) {
     const uint32_t b = blockIdx.x - r.blk0;
     const DevState* st = r.st;
     if (st->status != S_OK) return;
+    if (p.alpha >= 0.0 && !st->resample) return;  // partial: no resampling this step
     const int i = st->step + 1;
     const uint32_t Rprev = st->R_prev;
     uint64_t n;
@@ -448,7 +614,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scatter(KParams p) {
         if ((uint32_t)j >= Rprev) break;
         for (uint32_t c = 0; c < rc[e]; ++c) r.anc[o + c] = (uint32_t)j;
         o += rc[e];
-        const double tau = scalbn((double)f_of(j, r, dN, E, lmin), -FRAC_BITS);
+        const double tau = scalbn((double)f_of(j, p, r, st, dN, E, lmin), -FRAC_BITS);
         const double dl = __dsub_rn((double)rc[e], tau);
         sv = __dadd_rn(sv, __dmul_rn(dl, dl));
     }
@@ -507,6 +673,37 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
         r.partCL[b] = sd[0];
         if (sc2) atomicAdd(&r.trace[i].sumC2, sc2);
     }
+    if (p.alpha >= 0.0) {
+        // partial resampling: the new population's weights (1 after a
+        // resampling, else the kept weight rescaled by 2^-wexp), then the
+        // block's tree sums of w, w E, w E^2, w |M|, w M^2
+        __syncthreads();
+        const int32_t* Ec = r.E[i & 1];
+        double v[5][SCAN_ITEMS];
+#pragma unroll
+        for (int e = 0; e < SCAN_ITEMS; ++e) {
+            const uint32_t d = (uint32_t)(j0 + e);
+            double w = 0.0, E = 0.0, M = 0.0;
+            if (d < Ri) {
+                w = r.w[d];
+                if (mode == 0) {
+                    w = st->resample ? 1.0 : scalbn(w, -st->wexp);
+                    r.w[d] = w;
+                }
+                E = (double)Ec[d];
+                M = (double)r.M[d];
+            }
+            v[0][e] = w;
+            v[1][e] = __dmul_rn(w, E);
+            v[2][e] = __dmul_rn(w, __dmul_rn(E, E));
+            v[3][e] = __dmul_rn(w, fabs(M));
+            v[4][e] = __dmul_rn(w, __dmul_rn(M, M));
+        }
+        for (int q = 0; q < 5; ++q) {
+            const double root = tree_threads(tree8(v[q]), sd);
+            if (threadIdx.x == 0) r.opart[5 * b + q] = root;
+        }
+    }
 }
 
 // fixed-order sums of the per-block partials, close the step
@@ -514,7 +711,7 @@ __global__ void __launch_bounds__(256) k_finish(KParams p, int mode) {
     const RunDesc& r = p.runs[blockIdx.x];
     DevState* st = r.st;
     if (st->status != S_OK) return;
-    __shared__ double a[256], b[256];
+    __shared__ double a[256], b[256], ws[256];
     const int i = (mode == 0) ? st->step + 1 : st->step;
     const int nb_sv = (mode == 0) ? (int)((st->R_prev + SCAN_CHUNK - 1) / SCAN_CHUNK) : 0;
     const int nb_f = (int)((st->R_cur + SCAN_CHUNK - 1) / SCAN_CHUNK);
@@ -531,6 +728,24 @@ __global__ void __launch_bounds__(256) k_finish(KParams p, int mode) {
         }
         __syncthreads();
     }
+    if (p.alpha >= 0.0) {
+        // partial resampling: tree over the blocks' weighted sums (16 leaves
+        // per thread, PARTIAL_MAX_BLOCKS leaves in all, zero past the run's blocks)
+        const int nb = r.nblk;
+        for (int q = 0; q < 5; ++q) {
+            double x[16];
+            for (int k = 0; k < 16; ++k) {
+                const int bb = 16 * threadIdx.x + k;
+                x[k] = bb < nb ? r.opart[5 * bb + q] : 0.0;
+            }
+            const double root = tree_threads(__dadd_rn(tree8(x), tree8(x + 8)), ws);
+            if (threadIdx.x == 0) {
+                TraceRow* tr = r.trace + i;
+                double* dst[5] = {&tr->wsum, &tr->wE, &tr->wE2, &tr->wAM, &tr->wM2};
+                *dst[q] = root;
+            }
+        }
+    }
     if (threadIdx.x == 0) {
         TraceRow* tr = r.trace + i;
         tr->sv_sum = a[0];
@@ -544,10 +759,15 @@ __global__ void __launch_bounds__(256) k_finish(KParams p, int mode) {
 // --------------------------------------------------------------------------
 cudaError_t launch_resample(const KParams& p, cudaStream_t s, int64_t* launches) {
     k_weights<<<p.M, 1024, 0, s>>>(p);
+    int n = 4;
+    if (p.alpha >= 0.0) {
+        k_pw_update<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
+        k_pw_final<<<p.M, 1024, 0, s>>>(p);
+        n += 2;
+    }
     k_fsum<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
     k_fscan<<<p.M, 1024, 0, s>>>(p);
     k_counts<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
-    int n = 4;
     if (p.method == M_MULTINOMIAL || p.method == M_RESIDUAL) {
         k_draws<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
         ++n;
@@ -557,6 +777,11 @@ cudaError_t launch_resample(const KParams& p, cudaStream_t s, int64_t* launches)
     k_scatter<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
     n += 3;
     if (launches) *launches += n;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_partial_init(const KParams& p, cudaStream_t s) {
+    k_pw_init<<<dim3(64, (unsigned)p.M), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -48,10 +48,14 @@ __global__ void k_weighted(KParams p, const int32_t* run_ids, int n_runs, int n_
         const TraceRow& t = r.trace[i];
         const double w = exp(log((double)t.R_i) + t.sum_lnQ - amax) / S;
         const double Ri = (double)t.R_i;
-        const double e = (double)(long long)t.sumE / (Ri * N);
-        const double e2 = (double)(long long)t.sumE2 / (Ri * N * N);
-        const double am = (double)(long long)t.sumAbsM / (Ri * N);
-        const double m2 = (double)(long long)t.sumM2 / (Ri * N * N);
+        // per-run averages: plain, or weighted under partial resampling
+        const bool wtd = p.alpha >= 0.0 && t.wsum > 0.0;
+        const double e = wtd ? t.wE / (t.wsum * N) : (double)(long long)t.sumE / (Ri * N);
+        const double e2 =
+            wtd ? t.wE2 / (t.wsum * N * N) : (double)(long long)t.sumE2 / (Ri * N * N);
+        const double am = wtd ? t.wAM / (t.wsum * N) : (double)(long long)t.sumAbsM / (Ri * N);
+        const double m2 =
+            wtd ? t.wM2 / (t.wsum * N * N) : (double)(long long)t.sumM2 / (Ri * N * N);
         const double c = beta * beta * N * (e2 - e * e);
         const double x = beta * N * (m2 - am * am);
         We += w * e;

@@ -25,7 +25,7 @@ RESAMPLERS = {"multinomial": 0, "systematic": 1, "residual": 2, "poisson": 3, "n
 
 PA_COUPLING_FERRO, PA_COUPLING_EA_PM, PA_COUPLING_EXPLICIT = 0, 1, 2
 PA_ARRAY_SPINS, PA_ARRAY_ENERGY, PA_ARRAY_FAMILY = 0, 1, 2
-PA_ARRAY_COUNTS, PA_ARRAY_ANCESTOR, PA_ARRAY_MAGNET = 3, 4, 5
+PA_ARRAY_COUNTS, PA_ARRAY_ANCESTOR, PA_ARRAY_MAGNET, PA_ARRAY_WEIGHT = 3, 4, 5, 6
 
 EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observables", "pa_trace",
            "pa_free_energy", "pa_get_array", "pa_set_state", "pa_enable_timing",
@@ -34,7 +34,8 @@ EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observable
            "pa_batch_workspace_bytes", "pa_batch_init", "pa_batch_size", "pa_run_observables",
            "pa_run_trace", "pa_run_free_energy", "pa_run_get_array", "pa_weighted",
            "pa_set_graph", "pa_set_controller", "pa_schedule_taken", "pa_mlp_scratch_bytes",
-           "pa_mlp_forward", "pa_mlp_gradients", "pa_mlp_adam", "pa_overlap"]
+           "pa_mlp_forward", "pa_mlp_gradients", "pa_mlp_adam", "pa_overlap",
+           "pa_set_partial_resampling"]
 
 
 class pa_lattice(C.Structure):
@@ -60,10 +61,12 @@ class pa_obs(C.Structure):
                 ("e", C.c_double), ("e2", C.c_double), ("absm", C.c_double), ("m2", C.c_double),
                 ("c", C.c_double), ("chi", C.c_double), ("rho_t", C.c_double),
                 ("accept_rate", C.c_double), ("features", C.c_float * 8),
-                ("u_next", C.c_int32), ("theta_next", C.c_uint32)]
+                ("u_next", C.c_int32), ("theta_next", C.c_uint32), ("ess", C.c_double),
+                ("resampled", C.c_int32), ("pad1", C.c_int32)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad0", "features")}
+        d = {k: getattr(self, k) for k, _ in self._fields_
+             if k not in ("pad0", "pad1", "features")}
         d["features"] = list(self.features)
         return d
 
@@ -145,6 +148,7 @@ def _load():
     lib.pa_weighted.argtypes = [vp, C.c_int32, C.POINTER(pa_weighted_obs), C.c_int32,
                                 C.POINTER(C.c_int32)]
     lib.pa_set_graph.argtypes = [vp, C.c_int32]
+    lib.pa_set_partial_resampling.argtypes = [vp, C.c_double]
     lib.pa_overlap.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32,
                                vp, C.POINTER(C.c_double)]
     lib.pa_set_controller.argtypes = [vp, C.POINTER(pa_controller)]
@@ -267,7 +271,7 @@ def pa_free_energy(ctx):
 
 _ARRAY_DTYPE = {PA_ARRAY_SPINS: np.uint32, PA_ARRAY_ENERGY: np.int32, PA_ARRAY_FAMILY: np.uint32,
                 PA_ARRAY_COUNTS: np.uint32, PA_ARRAY_ANCESTOR: np.uint32,
-                PA_ARRAY_MAGNET: np.int32}
+                PA_ARRAY_MAGNET: np.int32, PA_ARRAY_WEIGHT: np.float64}
 
 
 def pa_get_array(ctx, which, capacity):
@@ -375,6 +379,10 @@ def pa_weighted(ctx, ensemble, max_rows) -> list:
 
 def pa_set_graph(ctx, on=True):
     _check(_lib.pa_set_graph(ctx, 1 if on else 0), "pa_set_graph")
+
+
+def pa_set_partial_resampling(ctx, alpha):
+    _check(_lib.pa_set_partial_resampling(ctx, float(alpha)), "pa_set_partial_resampling")
 
 
 def pa_overlap(ctx, run_a, run_b, hist_dev_ptr, N, weighted=True):
@@ -530,6 +538,12 @@ class Population:
     def magnetisations(self):
         return self.array(PA_ARRAY_MAGNET)
 
+    def weights(self):
+        return self.array(PA_ARRAY_WEIGHT)
+
+    def set_partial_resampling(self, alpha):
+        pa_set_partial_resampling(self.ctx, alpha)
+
 
 def default_capacity(R, resampler):
     if resampler in (PA_POISSON, PA_NEAREST, "poisson", "nearest"):
@@ -596,6 +610,9 @@ class Batch:
 
     def weighted(self, ensemble):
         return pa_weighted(self.ctx, ensemble, self.n_steps + 1)
+
+    def set_partial_resampling(self, alpha):
+        pa_set_partial_resampling(self.ctx, alpha)
 
     def overlap(self, pairs):
         """Overlap distribution of run pairs [(a, b), ...] at the current step:
