@@ -123,14 +123,20 @@ __device__ __forceinline__ double tree8(const double* a) {
 }
 
 __device__ double tree_threads(double v, double* sh) {
-    const int t = threadIdx.x, n = blockDim.x;
-    sh[t] = v;
+    // levels inside a warp by shuffles (lane t adds lane t + w for t a multiple
+    // of 2w: the same pairs as the tree), then the same over the warps' sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int w = 1; w < 32; w <<= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, w));
+    if (lane == 0) sh[warp] = v;
     __syncthreads();
-    for (int w = 1; w < n; w <<= 1) {
-        if ((t & (2 * w - 1)) == 0) sh[t] = __dadd_rn(sh[t], sh[t + w]);
-        __syncthreads();
+    if (warp == 0) {
+        double u = lane < nw ? sh[lane] : 0.0;
+        for (int w = 1; w < nw; w <<= 1) u = __dadd_rn(u, __shfl_down_sync(0xffffffffu, u, w));
+        if (lane == 0) sh[32] = u;
     }
-    const double root = sh[0];
+    __syncthreads();
+    const double root = sh[32];
     __syncthreads();
     return root;
 }
@@ -358,6 +364,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_fsum(KParams p) {
     const uint32_t b = blockIdx.x - r.blk0;
     const DevState* st = r.st;
     if (st->status != S_OK) return;
+    if (p.alpha >= 0.0 && !st->resample) return;  // partial: population kept
     __shared__ uint64_t sh[33];
     const int i = st->step + 1;
     const int32_t* E = r.E[(i - 1) & 1];
@@ -412,6 +419,7 @@ __global__ void __launch_bounds__(1024) k_fscan(KParams p) {
     const RunDesc& r = p.runs[blockIdx.x];
     DevState* st = r.st;
     if (st->status != S_OK) return;
+    if (p.alpha >= 0.0 && !st->resample) return;
     __shared__ uint64_t tA, tB;
     scan_partials(r.partA, r.offA, r.nblk, &tA);
     scan_partials(r.partB, r.offB, r.nblk, &tB);
@@ -439,6 +447,19 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_counts(KParams p) {
     const uint32_t Rprev = st->R_prev, lmin = st->lmin;
     const uint64_t T = st->T;
     const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    if (p.alpha >= 0.0 && !st->resample) {
+        // partial resampling keeps every replica once: identity counts and
+        // ancestors, no sampling variance (the scan kernels return at once)
+        for (int e = 0; e < SCAN_ITEMS; ++e) {
+            const int j = j0 + e;
+            if ((uint32_t)j < Rprev) {
+                r.counts[j] = 1u;
+                r.anc[j] = (uint32_t)j;
+            }
+        }
+        if (threadIdx.x == 0) r.partD[b] = 0.0;
+        return;
+    }
     uint64_t f[SCAN_ITEMS];
     uint64_t sf = 0, sg = 0;
 #pragma unroll
@@ -456,7 +477,6 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_counts(KParams p) {
     if (method == M_SYSTEMATIC)
         usys = philox(0u, DOM_RESAMPLE | (r.run << 8) | RULE_SYSTEMATIC, (uint32_t)i, 0u, p.k0, p.k1).x;
     bool kmax = false;
-    const bool keep = p.alpha >= 0.0 && !st->resample;  // partial: every replica once
 #pragma unroll 1
     for (int e = 0; e < SCAN_ITEMS; ++e) {
         const int j = j0 + e;
@@ -467,9 +487,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_counts(KParams p) {
         r.C[j] = cf;
         if (method == M_RESIDUAL) r.G[j] = cg;
         uint32_t cnt = 0;
-        if (keep) {
-            cnt = 1u;
-        } else if (method == M_NEAREST) {
+        if (method == M_NEAREST) {
             const uint4x x = philox((uint32_t)j, DOM_RESAMPLE | (r.run << 8) | RULE_NEAREST, (uint32_t)i, 0u,
                                     p.k0, p.k1);
             const uint64_t u40 = (((uint64_t)x.y << 32) | x.x) >> 24;
@@ -559,6 +577,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_rsum(KParams p) {
     const uint32_t b = blockIdx.x - r.blk0;
     const DevState* st = r.st;
     if (st->status != S_OK) return;
+    if (p.alpha >= 0.0 && !st->resample) return;
     __shared__ uint64_t sh[33];
     const uint32_t Rprev = st->R_prev;
     const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
@@ -576,6 +595,7 @@ __global__ void __launch_bounds__(1024) k_rscan(KParams p) {
     const RunDesc& r = p.runs[blockIdx.x];
     DevState* st = r.st;
     if (st->status != S_OK) return;
+    if (p.alpha >= 0.0 && !st->resample) return;  // R_i = R_{i-1}
     __shared__ uint64_t tA;
     scan_partials(r.partA, r.offA, r.nblk, &tA);
     __syncthreads();
@@ -591,6 +611,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scatter(KParams p) {
     const uint32_t b = blockIdx.x - r.blk0;
     const DevState* st = r.st;
     if (st->status != S_OK) return;
+    if (p.alpha >= 0.0 && !st->resample) return;  // identity written by k_counts
     __shared__ uint64_t sh[33];
     __shared__ double sd[SCAN_THREADS];
     const int i = st->step + 1;
