@@ -300,6 +300,26 @@ pa_status pa_weighted(pa_ctx *ctx, int32_t ensemble, pa_weighted_obs *rows, int3
                       int32_t *n_rows);
 
 
+/* One run's summary at one temperature step, for combining runs that were
+ * computed anywhere (other GPUs, other processes, other times). */
+typedef struct {
+    uint32_t R_i;          /* population size at the step                          */
+    uint32_t R;            /* nominal population size                              */
+    double sum_lnQ;        /* sum_{k<=i} ln Q_k                                     */
+    int64_t sumE, sumE2, sumAbsM, sumM2;  /* exact sums over the population         */
+    double wsum, wE, wE2, wAM, wM2;  /* weighted sums (partial resampling); wsum = 0 */
+                                     /* means: use the exact sums                   */
+} pa_run_row;
+
+/* Weighted average (Eq. weighted-averages, Eqs. Wvar_C, Wvar_Chi) of n_runs run
+ * summaries of one system (lattice of N sites) at inverse temperature beta;
+ * the same combination as pa_weighted, computed on the GPU.  rows: host array,
+ * n_runs entries (copied); out: host.  step is copied into out->step.  The
+ * call allocates and frees its device buffers and synchronises cuda_stream
+ * (nullable).  PA_ERR_ARG for a run with R_i = 0 or R = 0. */
+pa_status pa_weighted_rows(const pa_run_row *rows, int32_t n_runs, int32_t N, double beta,
+                           int32_t step, pa_weighted_obs *out, void *cuda_stream);
+
 /* Partial resampling (Sec. 3: resampling is needed only once the variance of
  * the importance weights grows too large).  Call after init, before the first
  * step.  Replicas then carry weights w_j (initially 1).  Each step multiplies

@@ -11,7 +11,10 @@
 //   the naive weighting sum_m omega c^(m), sum_m omega chi^(m), the plain
 //   means over runs, and the combined estimate of ln(Z_i / Z_0) as
 //   ln( sum_m R^(m) Zhat_m / sum_m R^(m) ).
-// One thread per step; runs are summed in index order (fixed order).
+// One thread per step; runs are summed in index order (fixed order).  The
+// same combination serves the runs of one batch (k_weighted, from the trace
+// rows) and runs summarised anywhere else, e.g. on other GPUs
+// (k_weighted_rows, from rows the caller passes in).
 #include <cmath>
 
 #include "../../include/pa.h"
@@ -19,59 +22,48 @@
 
 namespace pa {
 
-__global__ void k_weighted(KParams p, const int32_t* run_ids, int n_runs, int n_rows,
-                           pa_weighted_obs* out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_rows) return;
-    const RunDesc& r0 = p.runs[run_ids[0]];
-    const double N = (double)r0.N;
-    const double beta = p.beta[i];
+// what the combination needs of one run at one step
+struct RunMoments {
+    double Ri, Rnom, slnq;  // R_i, nominal R, sum of ln Q
+    double e, e2, am, m2;   // per-run averages (weighted under partial resampling)
+};
+
+template <class Get>
+__device__ pa_weighted_obs combine_runs(int n_runs, double N, double beta, int step, Get get) {
     double amax = -INFINITY, bmax = -INFINITY, Rnom = 0.0;
     for (int k = 0; k < n_runs; ++k) {
-        const RunDesc& r = p.runs[run_ids[k]];
-        const TraceRow& t = r.trace[i];
-        amax = fmax(amax, log((double)t.R_i) + t.sum_lnQ);
-        bmax = fmax(bmax, log((double)r.R) + t.sum_lnQ);
-        Rnom += (double)r.R;
+        const RunMoments r = get(k);
+        amax = fmax(amax, log(r.Ri) + r.slnq);
+        bmax = fmax(bmax, log(r.Rnom) + r.slnq);
+        Rnom += r.Rnom;
     }
     double S = 0.0, Sb = 0.0;
     for (int k = 0; k < n_runs; ++k) {
-        const RunDesc& r = p.runs[run_ids[k]];
-        const TraceRow& t = r.trace[i];
-        S += exp(log((double)t.R_i) + t.sum_lnQ - amax);
-        Sb += exp(log((double)r.R) + t.sum_lnQ - bmax);
+        const RunMoments r = get(k);
+        S += exp(log(r.Ri) + r.slnq - amax);
+        Sb += exp(log(r.Rnom) + r.slnq - bmax);
     }
     double We = 0, We2 = 0, Wam = 0, Wm2 = 0, cn = 0, xn = 0, w2 = 0, wmax = 0;
     double pe = 0, pc = 0, px = 0;
     for (int k = 0; k < n_runs; ++k) {
-        const RunDesc& r = p.runs[run_ids[k]];
-        const TraceRow& t = r.trace[i];
-        const double w = exp(log((double)t.R_i) + t.sum_lnQ - amax) / S;
-        const double Ri = (double)t.R_i;
-        // per-run averages: plain, or weighted under partial resampling
-        const bool wtd = p.alpha >= 0.0 && t.wsum > 0.0;
-        const double e = wtd ? t.wE / (t.wsum * N) : (double)(long long)t.sumE / (Ri * N);
-        const double e2 =
-            wtd ? t.wE2 / (t.wsum * N * N) : (double)(long long)t.sumE2 / (Ri * N * N);
-        const double am = wtd ? t.wAM / (t.wsum * N) : (double)(long long)t.sumAbsM / (Ri * N);
-        const double m2 =
-            wtd ? t.wM2 / (t.wsum * N * N) : (double)(long long)t.sumM2 / (Ri * N * N);
-        const double c = beta * beta * N * (e2 - e * e);
-        const double x = beta * N * (m2 - am * am);
-        We += w * e;
-        We2 += w * e2;
-        Wam += w * am;
-        Wm2 += w * m2;
+        const RunMoments r = get(k);
+        const double w = exp(log(r.Ri) + r.slnq - amax) / S;
+        const double c = beta * beta * N * (r.e2 - r.e * r.e);
+        const double x = beta * N * (r.m2 - r.am * r.am);
+        We += w * r.e;
+        We2 += w * r.e2;
+        Wam += w * r.am;
+        Wm2 += w * r.m2;
         cn += w * c;
         xn += w * x;
         w2 += w * w;
         wmax = fmax(wmax, w);
-        pe += e;
+        pe += r.e;
         pc += c;
         px += x;
     }
     pa_weighted_obs o;
-    o.step = i;
+    o.step = step;
     o.n_runs = n_runs;
     o.beta = beta;
     o.lnZ = bmax + log(Sb) - log(Rnom);
@@ -89,7 +81,51 @@ __global__ void k_weighted(KParams p, const int32_t* run_ids, int n_runs, int n_
     o.e_plain = pe / n_runs;
     o.c_plain = pc / n_runs;
     o.chi_plain = px / n_runs;
-    out[i] = o;
+    return o;
+}
+
+// per-run averages from the exact sums, or from the weighted sums if wsum > 0
+__device__ __forceinline__ RunMoments moments(double Ri, double Rnom, double slnq, double N,
+                                              long long sE, long long sE2, long long sAM,
+                                              long long sM2, double wsum, double wE,
+                                              double wE2, double wAM, double wM2) {
+    RunMoments m;
+    m.Ri = Ri;
+    m.Rnom = Rnom;
+    m.slnq = slnq;
+    const bool wtd = wsum > 0.0;
+    m.e = wtd ? wE / (wsum * N) : (double)sE / (Ri * N);
+    m.e2 = wtd ? wE2 / (wsum * N * N) : (double)sE2 / (Ri * N * N);
+    m.am = wtd ? wAM / (wsum * N) : (double)sAM / (Ri * N);
+    m.m2 = wtd ? wM2 / (wsum * N * N) : (double)sM2 / (Ri * N * N);
+    return m;
+}
+
+__global__ void k_weighted(KParams p, const int32_t* run_ids, int n_runs, int n_rows,
+                           pa_weighted_obs* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_rows) return;
+    const double N = (double)p.runs[run_ids[0]].N;
+    const bool partial = p.alpha >= 0.0;
+    out[i] = combine_runs(n_runs, N, p.beta[i], i, [&](int k) {
+        const RunDesc& r = p.runs[run_ids[k]];
+        const TraceRow& t = r.trace[i];
+        return moments((double)t.R_i, (double)r.R, t.sum_lnQ, N, (long long)t.sumE,
+                       (long long)t.sumE2, (long long)t.sumAbsM, (long long)t.sumM2,
+                       partial ? t.wsum : 0.0, t.wE, t.wE2, t.wAM, t.wM2);
+    });
+}
+
+__global__ void k_weighted_rows(const pa_run_row* rows, int n_runs, int N, double beta,
+                                int32_t step, pa_weighted_obs* out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const double Nd = (double)N;
+    out[0] = combine_runs(n_runs, Nd, beta, step, [&](int k) {
+        const pa_run_row& r = rows[k];
+        return moments((double)r.R_i, (double)r.R, r.sum_lnQ, Nd, (long long)r.sumE,
+                       (long long)r.sumE2, (long long)r.sumAbsM, (long long)r.sumM2, r.wsum,
+                       r.wE, r.wE2, r.wAM, r.wM2);
+    });
 }
 
 cudaError_t launch_weighted(const KParams& p, const int32_t* run_ids, int n_runs, int n_rows,
@@ -99,3 +135,33 @@ cudaError_t launch_weighted(const KParams& p, const int32_t* run_ids, int n_runs
 }
 
 }  // namespace pa
+
+using namespace pa;
+
+extern "C" pa_status pa_weighted_rows(const pa_run_row* rows, int32_t n_runs, int32_t N,
+                                      double beta, int32_t step, pa_weighted_obs* out,
+                                      void* cuda_stream) {
+    if (!rows || !out || n_runs < 1 || N < 1) return PA_ERR_ARG;
+    for (int k = 0; k < n_runs; ++k)
+        if (rows[k].R_i == 0 || rows[k].R == 0) return PA_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    pa_run_row* d_rows = nullptr;
+    pa_weighted_obs* d_out = nullptr;
+    if (cudaMalloc(&d_rows, sizeof(pa_run_row) * n_runs) != cudaSuccess) return PA_ERR_NOMEM;
+    if (cudaMalloc(&d_out, sizeof(pa_weighted_obs)) != cudaSuccess) {
+        cudaFree(d_rows);
+        return PA_ERR_NOMEM;
+    }
+    cudaError_t e = cudaMemcpyAsync(d_rows, rows, sizeof(pa_run_row) * n_runs,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        k_weighted_rows<<<1, 32, 0, s>>>(d_rows, n_runs, N, beta, step, d_out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, d_out, sizeof(pa_weighted_obs), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_rows);
+    cudaFree(d_out);
+    return e == cudaSuccess ? PA_OK : PA_ERR_CUDA;
+}

@@ -35,7 +35,7 @@ EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observable
            "pa_run_trace", "pa_run_free_energy", "pa_run_get_array", "pa_weighted",
            "pa_set_graph", "pa_set_controller", "pa_schedule_taken", "pa_mlp_scratch_bytes",
            "pa_mlp_forward", "pa_mlp_gradients", "pa_mlp_adam", "pa_overlap",
-           "pa_set_partial_resampling"]
+           "pa_set_partial_resampling", "pa_weighted_rows"]
 
 
 class pa_lattice(C.Structure):
@@ -86,6 +86,13 @@ class pa_weighted_obs(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pa_run_row(C.Structure):
+    _fields_ = [("R_i", C.c_uint32), ("R", C.c_uint32), ("sum_lnQ", C.c_double),
+                ("sumE", C.c_int64), ("sumE2", C.c_int64), ("sumAbsM", C.c_int64),
+                ("sumM2", C.c_int64), ("wsum", C.c_double), ("wE", C.c_double),
+                ("wE2", C.c_double), ("wAM", C.c_double), ("wM2", C.c_double)]
 
 
 PA_MLP_NPARAM = 4866
@@ -149,6 +156,8 @@ def _load():
                                 C.POINTER(C.c_int32)]
     lib.pa_set_graph.argtypes = [vp, C.c_int32]
     lib.pa_set_partial_resampling.argtypes = [vp, C.c_double]
+    lib.pa_weighted_rows.argtypes = [C.POINTER(pa_run_row), C.c_int32, C.c_int32, C.c_double,
+                                     C.c_int32, C.POINTER(pa_weighted_obs), vp]
     lib.pa_overlap.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32,
                                vp, C.POINTER(C.c_double)]
     lib.pa_set_controller.argtypes = [vp, C.POINTER(pa_controller)]
@@ -383,6 +392,27 @@ def pa_set_graph(ctx, on=True):
 
 def pa_set_partial_resampling(ctx, alpha):
     _check(_lib.pa_set_partial_resampling(ctx, float(alpha)), "pa_set_partial_resampling")
+
+
+def run_row(obs, R_nominal, partial=False, N=None):
+    """pa_run_row from a pa_obs dict (pa_observables / pa_run_observables / a trace row)."""
+    r = pa_run_row(int(obs["R_i"]), int(R_nominal), float(obs["sum_lnQ"]), int(obs["sumE"]),
+                   int(obs["sumE2"]), int(obs["sumAbsM"]), int(obs["sumM2"]), 0.0, 0.0, 0.0,
+                   0.0, 0.0)
+    if partial:
+        # the weighted averages rescaled to a weight sum of 1
+        r.wsum = 1.0
+        r.wE, r.wE2 = obs["e"] * N, obs["e2"] * N * N
+        r.wAM, r.wM2 = obs["absm"] * N, obs["m2"] * N * N
+    return r
+
+
+def pa_weighted_rows(rows, N, beta, step=0, stream=0) -> dict:
+    arr = (pa_run_row * len(rows))(*rows)
+    out = pa_weighted_obs()
+    _check(_lib.pa_weighted_rows(arr, len(rows), int(N), float(beta), int(step), C.byref(out),
+                                 C.c_void_p(stream)), "pa_weighted_rows")
+    return out.as_dict()
 
 
 def pa_overlap(ctx, run_a, run_b, hist_dev_ptr, N, weighted=True):

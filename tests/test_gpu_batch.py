@@ -146,3 +146,27 @@ def test_weighted_free_energy_of_many_small_runs_reaches_kaufman():
     assert abs(est - kf) / (L * L) < 2e-4
     assert 1.0 <= rows[n]["eff_runs"] <= 40.0
     b.close()
+
+
+def test_weighted_rows_equal_batch_weighted_averages():
+    """Runs summarised as rows (as when they ran on other GPUs) and combined by
+    pa_weighted_rows give pa_weighted's numbers bit for bit, and the oracle's."""
+    runs = [{"dim": 2, "L": 16, "R": 400} for _ in range(5)] + [{"dim": 2, "L": 16, "R": 900}]
+    n = 12
+    betas = np.linspace(0, 1.0, n + 1)
+    b = pa.Batch(runs, betas, np.full(n, 4, np.uint32), "nearest", 19)
+    b.step(n)
+    rows = [pa.run_row(b.observables(m), runs[m]["R"]) for m in range(len(runs))]
+    got = pa.pa_weighted_rows(rows, 256, float(betas[n]), n)
+    ref = b.weighted(0)[n]
+    for k in ("lnZ", "minus_beta_F", "e", "e2", "absm", "m2", "c", "chi", "c_naive",
+              "chi_naive", "e_plain", "c_plain", "chi_plain", "w_max", "eff_runs"):
+        assert got[k] == ref[k], k
+    assert got["step"] == n and got["n_runs"] == len(runs)
+    oref = weighted_row([b.observables(m) for m in range(len(runs))], [r["R"] for r in runs],
+                        256, float(betas[n]))
+    for k in ("lnZ", "e", "c", "chi"):
+        assert math.isclose(got[k], oref[k], rel_tol=1e-11, abs_tol=1e-12), k
+    with pytest.raises(pa.PAError):
+        pa.pa_weighted_rows([pa.pa_run_row()], 256, 1.0)
+    b.close()
