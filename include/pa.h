@@ -332,7 +332,7 @@ pa_status pa_weighted_rows(const pa_run_row *rows, int32_t n_runs, int32_t N, do
  * index in FP64, so counts and decisions are reproducible.  alpha in [0, 1]:
  * 0 never resamples (annealed importance sampling), 1 resamples whenever the
  * weights differ.  Observables become weighted averages (pa_obs).  Every run
- * of the batch needs R_cap <= 4096 x 2048; pa_set_state is then unavailable.
+ * of the batch needs R_cap <= 16384 x 512; pa_set_state is then unavailable.
  * PA_ERR_ARG for bad arguments or a context that has stepped. */
 pa_status pa_set_partial_resampling(pa_ctx *ctx, double alpha);
 

@@ -193,10 +193,11 @@ struct KParams {
 };
 
 // partial resampling: blocks of a run whose tree sums one CTA can finish
-constexpr int PARTIAL_MAX_BLOCKS = 4096;
+constexpr int PARTIAL_MAX_BLOCKS = 16384;
+static_assert(PARTIAL_MAX_BLOCKS % 1024 == 0, "leaves per thread of the final trees");
 
 constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_ITEMS = 2;
 constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
 
 }  // namespace pa

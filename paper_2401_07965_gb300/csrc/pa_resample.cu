@@ -117,9 +117,16 @@ __device__ __forceinline__ T block_excl_scan(T v, T* sh, T* total) {
 // balanced binary tree sums (adjacent pairs first) in explicitly rounded FP64:
 // over 8 or 16 consecutive values, and over the threads of a CTA (thread t =
 // leaf t, blockDim a power of two); the root ends in every thread
-__device__ __forceinline__ double tree8(const double* a) {
-    return __dadd_rn(__dadd_rn(__dadd_rn(a[0], a[1]), __dadd_rn(a[2], a[3])),
-                     __dadd_rn(__dadd_rn(a[4], a[5]), __dadd_rn(a[6], a[7])));
+template <int NL>
+__device__ __forceinline__ double tree_regs(const double* a) {
+    double t[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) t[k] = a[k];
+#pragma unroll
+    for (int w = 1; w < NL; w <<= 1)
+#pragma unroll
+        for (int k = 0; k + w < NL; k += 2 * w) t[k] = __dadd_rn(t[k], t[k + w]);
+    return t[0];
 }
 
 __device__ double tree_threads(double v, double* sh) {
@@ -279,9 +286,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_pw_update(KParams p) {
             mx = fmax(mx, wn[e]);
         }
     }
-    const double s_old = tree_threads(tree8(wo), sh);
-    const double s_new = tree_threads(tree8(wn), sh);
-    const double s2 = tree_threads(tree8(w2), sh);
+    const double s_old = tree_threads(tree_regs<SCAN_ITEMS>(wo), sh);
+    const double s_new = tree_threads(tree_regs<SCAN_ITEMS>(wn), sh);
+    const double s2 = tree_threads(tree_regs<SCAN_ITEMS>(w2), sh);
     mx = max_threads(mx, sh);
     if (threadIdx.x == 0) {
         r.wpart[4 * b + 0] = s_old;
@@ -298,15 +305,17 @@ __global__ void __launch_bounds__(1024) k_pw_final(KParams p) {
     if (st->status != S_OK) return;
     __shared__ double sh[1024];
     const int i = st->step + 1;
-    const int nb = r.nblk;  // <= PARTIAL_MAX_BLOCKS = 4 leaves x 1024 threads
+    const int nb = r.nblk;  // <= PARTIAL_MAX_BLOCKS = LEAVES leaves x 1024 threads
+    constexpr int LEAVES = PARTIAL_MAX_BLOCKS / 1024;
     double S[3];
     for (int q = 0; q < 3; ++q) {
-        double x[4];
-        for (int k = 0; k < 4; ++k) {
-            const int bb = 4 * threadIdx.x + k;
+        double x[LEAVES];
+#pragma unroll
+        for (int k = 0; k < LEAVES; ++k) {
+            const int bb = LEAVES * threadIdx.x + k;
             x[k] = bb < nb ? r.wpart[4 * bb + q] : 0.0;
         }
-        S[q] = tree_threads(__dadd_rn(__dadd_rn(x[0], x[1]), __dadd_rn(x[2], x[3])), sh);
+        S[q] = tree_threads(tree_regs<LEAVES>(x), sh);
     }
     double mx = 0.0;
     for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) mx = fmax(mx, r.wpart[4 * bb + 3]);
@@ -721,7 +730,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
             v[4][e] = __dmul_rn(w, __dmul_rn(M, M));
         }
         for (int q = 0; q < 5; ++q) {
-            const double root = tree_threads(tree8(v[q]), sd);
+            const double root = tree_threads(tree_regs<SCAN_ITEMS>(v[q]), sd);
             if (threadIdx.x == 0) r.opart[5 * b + q] = root;
         }
     }
@@ -750,16 +759,18 @@ __global__ void __launch_bounds__(256) k_finish(KParams p, int mode) {
         __syncthreads();
     }
     if (p.alpha >= 0.0) {
-        // partial resampling: tree over the blocks' weighted sums (16 leaves
-        // per thread, PARTIAL_MAX_BLOCKS leaves in all, zero past the run's blocks)
+        // partial resampling: tree over the blocks' weighted sums
+        // (PARTIAL_MAX_BLOCKS leaves in all, zero past the run's blocks)
         const int nb = r.nblk;
+        constexpr int LEAVES = PARTIAL_MAX_BLOCKS / 256;
         for (int q = 0; q < 5; ++q) {
-            double x[16];
-            for (int k = 0; k < 16; ++k) {
-                const int bb = 16 * threadIdx.x + k;
+            double x[LEAVES];
+#pragma unroll
+            for (int k = 0; k < LEAVES; ++k) {
+                const int bb = LEAVES * threadIdx.x + k;
                 x[k] = bb < nb ? r.opart[5 * bb + q] : 0.0;
             }
-            const double root = tree_threads(__dadd_rn(tree8(x), tree8(x + 8)), ws);
+            const double root = tree_threads(tree_regs<LEAVES>(x), ws);
             if (threadIdx.x == 0) {
                 TraceRow* tr = r.trace + i;
                 double* dst[5] = {&tr->wsum, &tr->wE, &tr->wE2, &tr->wAM, &tr->wM2};
