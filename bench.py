@@ -644,6 +644,8 @@ def run_overlap(args):
     import torch
     from paper_2401_07965_gb300 import pa
     L, R, n, S = 32, 100000, 100, 16
+    if args.case == "small":
+        n = 10  # profiling: a short anneal before the same overlap launch
     N = L * L
     betas = np.linspace(0.0, 3.0, n + 1)
     thetas = np.full(n, 25, np.uint32)
@@ -797,7 +799,7 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    if args.case == "small":
+    if args.case == "small" and args.workload == "headline":
         return run_small(args)
     if args.workload == "ea3d":
         return run_ea3d(args)
