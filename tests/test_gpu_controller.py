@@ -253,3 +253,23 @@ def test_trained_controller_beats_plain_schedule_at_equal_budget():
     rms_l = float(np.sqrt(np.mean(np.square(err_learned))))
     print(f"rms plain {rms_p:.3e} learned {rms_l:.3e}")
     assert rms_l < 0.85 * rms_p
+
+
+def test_controlled_run_under_graph_replay_equals_direct_launches():
+    """The controller kernel is part of the captured step: replaying the graph on a side
+    stream takes the same decisions and reaches the same state as direct launches."""
+    L, R, K = 16, 300, 120
+    bits = _test_params()
+    grid = np.linspace(0.0, 1.0, K + 1)
+    side = torch.cuda.Stream()
+    a = CT.controlled_run(2, L, ("ferro",), R, grid, 2, 6, bits, seed=8, stream=side)
+    b = CT.controlled_run(2, L, ("ferro",), R, grid, 2, 6, bits, seed=8)
+    CT.run_to_end(a)
+    CT.run_to_end(b)
+    ba, ta = pa.pa_schedule_taken(a.ctx, K + 1)
+    bb, tb = pa.pa_schedule_taken(b.ctx, K + 1)
+    assert np.array_equal(ba, bb) and np.array_equal(ta, tb)
+    assert np.array_equal(a.spins_words(), b.spins_words())
+    assert a.observables()["sum_lnQ"] == b.observables()["sum_lnQ"]
+    a.close()
+    b.close()

@@ -137,3 +137,23 @@ def test_partial_resampling_arguments():
     with pytest.raises(pa.PAError):       # only before the first step
         p.set_partial_resampling(0.5)
     p.close()
+
+
+def test_partial_resampling_under_graph_replay_equals_direct_launches():
+    import torch
+    runs = [{"dim": 2, "L": 16, "R": 500}, {"dim": 2, "L": 16, "R": 300}]
+    betas = np.linspace(0.0, 1.0, 21)
+    th = np.full(20, 3, np.uint32)
+    a = pa.Batch(runs, betas, th, "nearest", 6, stream=torch.cuda.Stream(), graph=True)
+    b = pa.Batch(runs, betas, th, "nearest", 6, graph=False)
+    a.set_partial_resampling(0.5)
+    b.set_partial_resampling(0.5)
+    a.step(20)
+    for _ in range(20):
+        b.step(1)
+    for m in range(2):
+        assert np.array_equal(a.spins_words(m), b.spins_words(m))
+        assert np.array_equal(a.array(m, pa.PA_ARRAY_WEIGHT), b.array(m, pa.PA_ARRAY_WEIGHT))
+        assert a.observables(m) == b.observables(m)
+    a.close()
+    b.close()
