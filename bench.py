@@ -500,12 +500,34 @@ def run_accuracy(args):
                              "max_err_per_spin": float(max(errs))})
         ok = [g for g in grid if g["max_err_per_spin"] <= 1e-4]
         out[L] = {"best": min(ok, key=lambda g: g["ms"]) if ok else None, "grid": grid}
+    # the learned schedule on the same lattice: grid of R and total sweeps, 800-point grid
+    from paper_2401_07965_gb300 import controller as CT
+    learned = None
+    if os.path.exists(CT.WEIGHTS):
+        bits = CT.load()
+        L, K = 64, 800
+        exact = _kaufman(L, 1.0)
+        grid_l = []
+        for R in (3000, 10000, 30000):
+            for budget in (500, 1000, 2000):
+                errs, times = [], []
+                for seed in (11, 12, 13, 14, 15):
+                    pop = CT.controlled_run(2, L, ("ferro",), R, np.linspace(0.0, 1.0, K + 1), 4,
+                                            10, bits, seed=seed, budget=budget, stream=stream)
+                    times.append(_chunked(pa, pop, stream, K))
+                    mbf, _ = pop.free_energy()
+                    errs.append(abs(mbf - exact) / (L * L))
+                    pop.close()
+                grid_l.append({"R": R, "sweeps": budget, "ms": float(np.mean(times)),
+                               "max_err_per_spin": float(max(errs))})
+        ok = [g for g in grid_l if g["max_err_per_spin"] <= 1e-4]
+        learned = {"best": min(ok, key=lambda g: g["ms"]) if ok else None, "grid": grid_l}
     best = out[64]["best"]
     _line("time to |f - f_exact| <= 1e-4 per spin at beta=1, 2D Ising L=64 (200 steps) and "
           "L=16 (100 steps), systematic, worst of 5 seeds", best["ms"] if best else None,
           best["ms"] if best else 0.0, 200, 0,
           {"unit": "ms", "higher_is_better": False, "best": best, "grid": out[64]["grid"],
-           "L16": out[16]})
+           "L16": out[16], "learned_schedule_L64": learned})
     return 0
 
 
