@@ -49,14 +49,15 @@ WORKLOAD = ("2D Ising ferromagnet L=64 periodic, R=100000, beta 0->1 in 200 step
 # E_B = sum_g P(some replica undecided after 4g planes) = sum_g 1-(1-16^-g)^32.
 # Per block: 14 wide multiplies (rounds 4-10; rounds 1-3 are shared by the
 # counter layout) and 17 ALU operations (their 14 three-input XORs and 3 to
-# combine the shared halves), plus 5 ALU operations per plane (threshold mask
-# of the replica classes, the "less" and the "undecided" update) for d = 2.
+# combine the shared halves), plus 4 ALU operations per plane (threshold bits of
+# the replica classes: 2; the borrow and the "equal so far" update: 1 each) for
+# d = 2.
 # Per site: 2 wide multiplies (rounds 2-3) and 12 ALU operations (four
 # neighbour XORs, the class masks, the flip).  ALU operations run on a pipe of
 # 64 lanes per clock per SM (ncu: sm__inst_executed_pipe_alu peak = 2 warp
 # instructions per cycle); wide multiplies on one of 32 per clock (probe).
 E_BLOCKS = sum(1.0 - (1.0 - 16.0 ** -g) ** 32 for g in range(8))
-ALU_OPS_PER_SITEWORD = 12 + E_BLOCKS * (17 + 4 * 5)
+ALU_OPS_PER_SITEWORD = 12 + E_BLOCKS * (17 + 4 * 4)
 MULWIDE_PER_SITEWORD = 2 + E_BLOCKS * 14
 ALU_OPS_PER_UPDATE = ALU_OPS_PER_SITEWORD / 32.0
 MULWIDE_PER_UPDATE = MULWIDE_PER_SITEWORD / 32.0
