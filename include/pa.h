@@ -54,7 +54,8 @@ typedef enum {
     PA_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                          */
     PA_ERR_STATE = 7,         /* the context holds an earlier device error              */
     PA_ERR_DONE = 8,          /* the schedule has no further temperature step           */
-    PA_ERR_LIMIT = 9          /* a size exceeds the fixed limit of pa_weights_static    */
+    PA_ERR_LIMIT = 9          /* a size exceeds a fixed limit: R or R_cap >= 2^24, or the */
+                              /* scratch limit of pa_weights_static                     */
 } pa_status;
 
 /* Copy-count rules of Sec. 3.  Multinomial, systematic and residual keep
@@ -181,8 +182,11 @@ size_t pa_workspace_bytes(const pa_lattice *lat, uint32_t R, uint32_t R_cap, int
  * cuda_stream: a cudaStream_t (may be NULL).
  * workspace / workspace_bytes: optional caller-owned device memory (256-byte
  * aligned, at least pa_workspace_bytes) or NULL / 0.
+ * R and R_cap are below 2^24: the expected copy numbers are 2^-40 fixed-point
+ * integers whose total, R 2^40, must fit in 64 bits.
  * Errors: PA_ERR_ARG (bad lattice, R == 0, R_cap < R, schedule not starting
- * at 0 or not increasing, theta too large), PA_ERR_NOMEM, PA_ERR_CUDA. */
+ * at 0 or not increasing, theta too large), PA_ERR_LIMIT (R or R_cap >= 2^24),
+ * PA_ERR_NOMEM, PA_ERR_CUDA. */
 pa_status pa_init(pa_ctx **out, const pa_lattice *lat, const pa_couplings *cpl, uint32_t R,
                   uint32_t R_cap, const pa_schedule *sched, pa_resampler resampler,
                   uint64_t seed, void *cuda_stream, void *workspace, size_t workspace_bytes);
@@ -237,6 +241,15 @@ int64_t pa_launch_count(const pa_ctx *ctx);
 pa_status pa_set_sweep_threads(pa_ctx *ctx, int32_t threads);
 int32_t pa_get_sweep_threads(const pa_ctx *ctx);
 
+/* Test hook of the sweep kernel (Sec. 2 step 3): per half-sweep the kernel
+ * queues the sites whose Metropolis test is still undecided after the first
+ * eight bits of the uniforms and finishes them in a second pass; sites that
+ * find the queue full finish at once.  cap limits the queue to cap entries
+ * (0: every site finishes at once; -1: the kernel's full queue, the default)
+ * so that both paths can be checked.  Results do not depend on it.
+ * PA_ERR_ARG for cap < -1. */
+pa_status pa_set_sweep_queue(pa_ctx *ctx, int32_t cap);
+
 /* Reweighting of one temperature step without any device allocation.
  *
  * Some callers cannot call cudaMalloc: code embedded in a host framework that
@@ -251,23 +264,27 @@ int32_t pa_get_sweep_threads(const pa_ctx *ctx);
  * From the energies E[0..R_prev) (device, int32, each a valid energy of the
  * dim-dimensional periodic L^dim lattice whose number of J = -1 bonds has the
  * given parity), for the step dbeta = beta_i - beta_{i-1} > 0 it writes
- *   *lnQ (device double)          ln Q_i of Eq. (Q), the same bits as pa_step,
- *   f[0..R_prev) (device uint64)  floor(2^40 tau-hat_j), tau-hat of Eq. (taus)
- *                                 with nominal size R,
+ *   *lnQ (device double)          ln Q_i, the same bits as pa_step computes,
+ *   f[0..R_prev) (device uint64)  floor(2^40 R w_j / sum_k w_k), w_j the
+ *                                 Boltzmann factor of E_j at dbeta: the
+ *                                 fixed-point expected copy numbers of pa_step
+ *                                 for nominal size R,
  * asynchronously on cuda_stream (NULL = legacy default stream).  If an energy
- * lies outside the lattice's range, *lnQ is set to NaN and f is not written.
+ * is not a valid one (outside [-dim N, dim N], or (E + dim N)/2 not an integer
+ * of the given parity), *lnQ is set to NaN and f is not written.
  *
  * Scratch: one statically allocated device array (about 1.3 MB) that every
  * GPU loading the library holds until the process exits.  Every call shares
  * it and it keeps the last call's contents (the call clears what must start
  * at zero), so calls whose kernels overlap on the GPU -- on different streams,
  * or from several host threads -- race and must be serialised by the caller.
- * The first call on each device looks up the array's device address with that
- * device current; make that first call before any stream capture begins.
+ * Each call looks up the array's device address with the caller's device
+ * current; the first call on a device loads the library's device code there,
+ * so make that first call before any stream capture begins.
  *
- * Limits: dim*N/2 + 1 <= 65536 energy levels and N <= 32768 sites, else
- * PA_ERR_LIMIT; other bad arguments give PA_ERR_ARG.  No cudaMalloc, cudaFree
- * or allocating library routine is called. */
+ * Limits: dim*N/2 + 1 <= 65536 energy levels, N <= 32768 sites and R < 2^24,
+ * else PA_ERR_LIMIT; other bad arguments give PA_ERR_ARG.  No cudaMalloc,
+ * cudaFree or allocating library routine is called. */
 pa_status pa_weights_static(const int32_t *E, uint32_t R_prev, uint32_t R, int32_t dim, int32_t L,
                             int32_t parity, double dbeta, double *lnQ, uint64_t *f,
                             void *cuda_stream);
@@ -344,7 +361,8 @@ pa_status pa_set_partial_resampling(pa_ctx *ctx, double alpha);
  * j < min(R_i^a, R_i^b); the pair's overlap is q = (1/N) sum_s s^a_s s^b_s =
  * 1 - 2k/N with k the number of sites where the two differ.
  *   hist_dev: device array of n_pairs x (N+1) uint32, caller-owned, row-major;
- *             overwritten with the number of replica pairs at each k.
+ *             overwritten with the number of replica pairs at each k (a row
+ *             whose runs hold a device error is not written).
  *   P_out:    host array of N+1 doubles, or NULL.  When given, receives the
  *             weighted estimate P(k) = sum_p omega_p hist_p[k] / n_p with
  *             omega_p proportional to (R_i^a Zhat_a)(R_i^b Zhat_b), the product

@@ -18,7 +18,7 @@ cudaError_t launch_weighted(const KParams& p, const int32_t* run_ids, int n_runs
                             pa_weighted_obs* out, cudaStream_t s);
 cudaError_t launch_overlap(const KParams& p, const int32_t* pairs, int n_pairs, int Wp,
                            uint32_t max_rows, int bins, uint32_t* hist, double* P,
-                           cudaStream_t s);
+                           uint32_t* acc, uint32_t* tickets, cudaStream_t s);
 }
 
 using namespace pa;
@@ -41,7 +41,7 @@ enum Region {
 
 enum Shared {
     S_RUNS, S_B2R, S_G2R, S_BETA, S_DBETA, S_Q, S_THR, S_THETA, S_IDS, S_WOUT,
-    S_CTL, S_GBETA, S_GTHR, S_GDB, S_GQ, S_PAIRS, S_POV, S_COUNT
+    S_CTL, S_GBETA, S_GTHR, S_GDB, S_GQ, S_PAIRS, S_POV, S_OVACC, S_OVTICK, S_COUNT
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -73,7 +73,8 @@ struct pa_ctx {
     cudaGraphExec_t graph = nullptr;
     int graph_threads = 0;
     int64_t graph_kernels = 0;
-    std::vector<cudaEvent_t> ev_start, ev_stop;
+    std::vector<cudaEvent_t> ev_start, ev_stop;  // pool of timing events, reused
+    size_t ev_used = 0;
     std::vector<int> timed_steps;
     std::vector<double> beta;
     std::vector<uint32_t> theta;
@@ -81,6 +82,9 @@ struct pa_ctx {
     pa_weighted_obs* d_wout = nullptr;      // its output rows (device)
     int32_t* d_pairs = nullptr;             // run pairs for pa_overlap (device)
     double* d_pov = nullptr;                // its weighted P(q) (device)
+    uint32_t* d_ovacc = nullptr;            // its per-pair accumulators (zero between calls)
+    uint32_t* d_ovtick = nullptr;           // and per-pair CTA tickets (zero between calls)
+    std::vector<int32_t> pairs_cached;      // the pair list currently in d_pairs
     bool controlled = false;                // learned schedule active
     bool finished = false;                  // beta_f reached under the controller
     CtlDev* d_ctl = nullptr;
@@ -107,22 +111,26 @@ uint32_t default_cap(uint32_t R, int method) {
     return R;
 }
 
-// geometry and sizes of each run; couplings are filled by fill_couplings
-bool make_runs(const pa_run_spec* specs, int M, int method, std::vector<RunHost>* out, int* d) {
-    if (!specs || M < 1 || M > (1 << 20) || method < 0 || method > 4) return false;
+// geometry and sizes of each run; couplings are filled by fill_couplings.
+// PA_ERR_LIMIT for a population or capacity of 2^24 or more, PA_ERR_ARG for
+// other invalid specifications.
+pa_status make_runs(const pa_run_spec* specs, int M, int method, std::vector<RunHost>* out,
+                    int* d) {
+    if (!specs || M < 1 || M > (1 << 20) || method < 0 || method > 4) return PA_ERR_ARG;
     out->clear();
     for (int m = 0; m < M; ++m) {
         const pa_run_spec& s = specs[m];
         long long N;
-        if (!check_lattice(&s.lattice, &N)) return false;
+        if (!check_lattice(&s.lattice, &N)) return PA_ERR_ARG;
         if (m == 0) *d = s.lattice.dim;
-        if (s.lattice.dim != *d) return false;
-        if (s.R == 0 || s.ensemble < 0) return false;
-        if (s.couplings.kind < 0 || s.couplings.kind > 2) return false;
+        if (s.lattice.dim != *d) return PA_ERR_ARG;
+        if (s.R == 0 || s.ensemble < 0) return PA_ERR_ARG;
+        if (s.couplings.kind < 0 || s.couplings.kind > 2) return PA_ERR_ARG;
         if ((s.couplings.kind == PA_COUPLING_FERRO) !=
             (specs[0].couplings.kind == PA_COUPLING_FERRO))
-            return false;
-        if (s.couplings.kind == PA_COUPLING_EXPLICIT && !s.couplings.J) return false;
+            return PA_ERR_ARG;
+        if (s.couplings.kind == PA_COUPLING_EXPLICIT && !s.couplings.J) return PA_ERR_ARG;
+        if (s.R > MAX_POPULATION || s.R_cap > MAX_POPULATION) return PA_ERR_LIMIT;
         RunHost h;
         h.L = s.lattice.L;
         h.N = (int)N;
@@ -133,14 +141,15 @@ bool make_runs(const pa_run_spec* specs, int M, int method, std::vector<RunHost>
         while (h.P < h.nlev) h.P <<= 1;
         h.R = s.R;
         h.Rcap = s.R_cap ? s.R_cap : default_cap(s.R, method);
-        if (h.Rcap < h.R || h.Rcap > (1u << 30)) return false;
+        if (h.Rcap < h.R) return PA_ERR_ARG;
+        if (h.Rcap > MAX_POPULATION) return PA_ERR_LIMIT;
         h.nblk = (int)((h.Rcap + SCAN_CHUNK - 1) / SCAN_CHUNK);
         h.ngrp = (int)((h.Rcap + 31) / 32);
         h.ensemble = s.ensemble;
         h.parity = 0;
         out->push_back(std::move(h));
     }
-    return true;
+    return PA_OK;
 }
 
 Layout make_layout(const std::vector<RunHost>& runs, int n_steps) {
@@ -169,6 +178,8 @@ Layout make_layout(const std::vector<RunHost>& runs, int n_steps) {
     for (const RunHost& h : runs) maxN = h.N > maxN ? h.N : maxN;
     sz[S_PAIRS] = M * 2 * 4;
     sz[S_POV] = (size_t)(maxN + 1) * 8;
+    sz[S_OVACC] = M * (size_t)(maxN + 1) * 4;  // overlap accumulators, zero between calls
+    sz[S_OVTICK] = M * 4;
     size_t o = 0;
     for (int r = 0; r < S_COUNT; ++r) {
         L.shared_off[r] = o;
@@ -405,6 +416,22 @@ bool valid_schedule(const pa_schedule* sched) {
 
 bool valid_run(const pa_ctx* ctx, int run) { return ctx && run >= 0 && run < ctx->M; }
 
+// n more start/stop event pairs for timing mode (created outside the timed steps)
+pa_status grow_event_pool(pa_ctx* ctx, size_t n) {
+    for (size_t k = 0; k < n; ++k) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        PA_CUDA(cudaEventCreate(&a));
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            ctx->sticky = PA_ERR_CUDA;
+            return PA_ERR_CUDA;
+        }
+        ctx->ev_start.push_back(a);
+        ctx->ev_stop.push_back(b);
+    }
+    return PA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -413,7 +440,7 @@ size_t pa_batch_workspace_bytes(const pa_run_spec* runs, int32_t M, int32_t n_st
                                 pa_resampler resampler) {
     std::vector<RunHost> rh;
     int d = 0;
-    if (n_steps < 1 || !make_runs(runs, M, (int)resampler, &rh, &d)) return 0;
+    if (n_steps < 1 || make_runs(runs, M, (int)resampler, &rh, &d) != PA_OK) return 0;
     return make_layout(rh, n_steps).total;
 }
 
@@ -437,7 +464,8 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     if (!valid_schedule(sched)) return PA_ERR_ARG;
     std::vector<RunHost> rh;
     int d = 0;
-    if (!make_runs(specs, M, (int)resampler, &rh, &d)) return PA_ERR_ARG;
+    const pa_status ms = make_runs(specs, M, (int)resampler, &rh, &d);
+    if (ms != PA_OK) return ms;
     for (int m = 0; m < M; ++m)
         if (!fill_couplings(rh[m], d, specs[m].couplings)) return PA_ERR_ARG;
     const int n = sched->n_steps;
@@ -503,6 +531,8 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     ctx->d_wout = (pa_weighted_obs*)(base + lay.shared_off[S_WOUT]);
     ctx->d_pairs = (int32_t*)(base + lay.shared_off[S_PAIRS]);
     ctx->d_pov = (double*)(base + lay.shared_off[S_POV]);
+    ctx->d_ovacc = (uint32_t*)(base + lay.shared_off[S_OVACC]);
+    ctx->d_ovtick = (uint32_t*)(base + lay.shared_off[S_OVTICK]);
     p.beta_rw = (double*)p.beta;
     p.dbeta_rw = (double*)p.dbeta;
     p.q_rw = (double*)p.q;
@@ -510,6 +540,7 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     p.theta_rw = (uint32_t*)p.theta;
     p.ctl = nullptr;
     p.alpha = -1.0;
+    p.qcap_limit = -1;
     ctx->d_ctl = (CtlDev*)(base + lay.shared_off[S_CTL]);
     ctx->d_gbeta = (double*)(base + lay.shared_off[S_GBETA]);
     ctx->d_gthr = (uint32_t*)(base + lay.shared_off[S_GTHR]);
@@ -612,6 +643,9 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
         if (e == cudaSuccess) e = cudaMemsetAsync(r.counts, 0, (size_t)h.Rcap * 4, ctx->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(r.anc, 0, (size_t)h.Rcap * 4, ctx->stream);
     }
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ctx->d_ovacc, 0, (size_t)M * (maxN + 1) * 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_ovtick, 0, (size_t)M * 4, ctx->stream);
     if (e == cudaSuccess) e = launch_init_spins(p, ctx->desc.data(), ctx->stream);
     if (e != cudaSuccess) {
         pa_destroy(ctx);
@@ -667,11 +701,12 @@ pa_status pa_step(pa_ctx* ctx, int32_t n) {
             ctx->launches += ctx->graph_kernels;
         } else if (ctx->timing) {
             PA_CUDA(launch_resample(ctx->kp, ctx->stream, &ctx->launches));
-            cudaEvent_t a, b;
-            PA_CUDA(cudaEventCreate(&a));
-            PA_CUDA(cudaEventCreate(&b));
-            ctx->ev_start.push_back(a);
-            ctx->ev_stop.push_back(b);
+            if (ctx->ev_used == ctx->ev_start.size()) {
+                const pa_status ps = grow_event_pool(ctx, 1);
+                if (ps != PA_OK) return ps;
+            }
+            cudaEvent_t a = ctx->ev_start[ctx->ev_used], b = ctx->ev_stop[ctx->ev_used];
+            ctx->ev_used += 1;
             ctx->timed_steps.push_back(i);
             PA_CUDA(cudaEventRecord(a, ctx->stream));
             PA_CUDA(launch_sweep(ctx->kp, ctx->threads, ctx->stream));
@@ -906,10 +941,15 @@ pa_status pa_overlap(pa_ctx* ctx, const int32_t* run_a, const int32_t* run_b, in
         pairs[2 * q + 1] = b;
         rows = std::max(rows, std::min(ctx->runs[a].Rcap, ctx->runs[b].Rcap));
     }
-    PA_CUDA(cudaMemcpyAsync(ctx->d_pairs, pairs.data(), pairs.size() * 4, cudaMemcpyHostToDevice,
-                            ctx->stream));
+    if (pairs != ctx->pairs_cached) {  // the device copy of the pair list is kept
+        PA_CUDA(cudaMemcpyAsync(ctx->d_pairs, pairs.data(), pairs.size() * 4,
+                                cudaMemcpyHostToDevice, ctx->stream));
+        PA_CUDA(cudaStreamSynchronize(ctx->stream));  // the host vector is temporary
+        ctx->pairs_cached = pairs;
+    }
     PA_CUDA(launch_overlap(ctx->kp, ctx->d_pairs, n_pairs, ctx->runs[run_a[0]].Wp, rows, N + 1,
-                           hist_dev, P_out ? ctx->d_pov : nullptr, ctx->stream));
+                           hist_dev, P_out ? ctx->d_pov : nullptr, ctx->d_ovacc, ctx->d_ovtick,
+                           ctx->stream));
     ctx->launches += P_out ? 2 : 1;
     if (!P_out) return PA_OK;  // asynchronous on the context's stream
     pa_status st = pa_sync(ctx);
@@ -1029,6 +1069,11 @@ pa_status pa_set_graph(pa_ctx* ctx, int32_t on) {
 pa_status pa_enable_timing(pa_ctx* ctx, int32_t on) {
     if (!ctx) return PA_ERR_ARG;
     ctx->timing = on != 0;
+    if (ctx->timing) {
+        // one event pair per remaining step, created now rather than inside pa_step
+        const size_t want = ctx->ev_used + (size_t)(ctx->n_steps - ctx->host_step);
+        if (want > ctx->ev_start.size()) return grow_event_pool(ctx, want - ctx->ev_start.size());
+    }
     return PA_OK;
 }
 
@@ -1043,21 +1088,18 @@ pa_status pa_sweep_timing(pa_ctx* ctx, double* ms, int64_t* launches, double* up
         PA_CUDA(cudaMemcpy(t[m].data(), ctx->desc[m].trace, sizeof(TraceRow) * t[m].size(),
                            cudaMemcpyDeviceToHost));
     }
-    for (size_t k = 0; k < ctx->ev_start.size(); ++k) {
+    for (size_t k = 0; k < ctx->ev_used; ++k) {
         float f = 0.f;
         PA_CUDA(cudaEventElapsedTime(&f, ctx->ev_start[k], ctx->ev_stop[k]));
         total += f;
         const int i = ctx->timed_steps[k];
         for (int m = 0; m < ctx->M; ++m)
             upd += (double)ctx->theta[i - 1] * (double)ctx->runs[m].N * (double)t[m][i].R_i;
-        cudaEventDestroy(ctx->ev_start[k]);
-        cudaEventDestroy(ctx->ev_stop[k]);
     }
     if (ms) *ms = total;
-    if (launches) *launches = (int64_t)ctx->ev_start.size();
+    if (launches) *launches = (int64_t)ctx->ev_used;
     if (updates) *updates = upd;
-    ctx->ev_start.clear();
-    ctx->ev_stop.clear();
+    ctx->ev_used = 0;  // the pool is kept for the next timed steps
     ctx->timed_steps.clear();
     return PA_OK;
 }
@@ -1071,6 +1113,16 @@ pa_status pa_set_sweep_threads(pa_ctx* ctx, int32_t threads) {
 }
 
 int32_t pa_get_sweep_threads(const pa_ctx* ctx) { return ctx ? ctx->threads : 0; }
+
+pa_status pa_set_sweep_queue(pa_ctx* ctx, int32_t cap) {
+    if (!ctx || cap < -1) return PA_ERR_ARG;
+    ctx->kp.qcap_limit = cap;
+    if (ctx->graph) {  // the captured step holds the old kernel parameters
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return PA_OK;
+}
 
 pa_status pa_destroy(pa_ctx* ctx) {
     if (!ctx) return PA_OK;
@@ -1095,7 +1147,7 @@ const char* pa_strerror(pa_status s) {
         case PA_ERR_TIMEOUT: return "a bounded device wait timed out";
         case PA_ERR_STATE: return "context holds an earlier error";
         case PA_ERR_DONE: return "schedule exhausted";
-        case PA_ERR_LIMIT: return "size exceeds the static scratch limit of pa_weights_static";
+        case PA_ERR_LIMIT: return "size exceeds a fixed limit of the library";
         default: return "unknown status";
     }
 }

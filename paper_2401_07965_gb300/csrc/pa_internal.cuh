@@ -35,6 +35,9 @@ constexpr uint32_t RULE_NEAREST = 0u, RULE_SYSTEMATIC = 1u, RULE_MULTINOMIAL = 2
                    RULE_RESIDUAL = 3u, RULE_POISSON = 4u;
 
 constexpr int FRAC_BITS = 40;          // tau-hat is carried as a 2^-40 fixed-point integer
+// tau-hat_j <= R, so f_j = floor(2^40 tau-hat_j) and T = sum_j f_j <= R 2^40 fit in
+// 64 bits only for R < 2^24: the largest nominal population (and capacity)
+constexpr uint32_t MAX_POPULATION = (1u << 24) - 1u;
 constexpr uint32_t POISSON_KMAX = 256; // per chunk of mean <= 16
 
 enum Method { M_MULTINOMIAL = 0, M_SYSTEMATIC = 1, M_RESIDUAL = 2, M_POISSON = 3, M_NEAREST = 4 };
@@ -190,6 +193,7 @@ struct KParams {
     uint32_t* theta_rw;
     const CtlDev* ctl;       // null without a controller
     double alpha;            // partial resampling threshold (< 0: resample every step)
+    int qcap_limit;          // sweep: cap on the undecided-site queue (< 0: its full size)
 };
 
 // partial resampling: blocks of a run whose tree sums one CTA can finish

@@ -9,9 +9,13 @@
 //
 // k_overlap_hist: G lanes per replica pair read the two rows with coalesced
 // 128-bit loads, add the popcounts, reduce with shuffles, and one lane counts
-// the pair in the CTA's shared-memory histogram, which is added to hist[p][k]
-// at the end (counts are exact integers).  The kernel is bound by HBM: 2 Wp
-// words per replica pair are read once.
+// the pair in the CTA's shared-memory histogram, which is added to the pair's
+// accumulator in the context's workspace at the end (counts are exact
+// integers).  The last CTA of a pair to finish (a ticket counter) moves the
+// accumulator into the caller's hist[p][k] with plain stores and leaves the
+// accumulator and the ticket at zero for the next call, so no separate zeroing
+// pass is needed.  The kernel is bound by HBM: 2 Wp words per replica pair are
+// read once.
 //
 // k_overlap_P: one thread per k; the weighted estimate over pairs,
 //   P(k) = sum_p omega_p hist_p[k] / n_p,  omega_p ∝ (R_i^a Zhat_a)(R_i^b Zhat_b),
@@ -31,8 +35,10 @@ namespace pa {
 template <bool SMEM_HIST>
 __global__ void __launch_bounds__(256) k_overlap_hist(KParams p, const int32_t* pairs,
                                                       int lanes_per_pair, int bins,
-                                                      uint32_t* hist) {
+                                                      uint32_t* hist, uint32_t* acc_all,
+                                                      uint32_t* tickets) {
     extern __shared__ uint32_t sh[];
+    __shared__ int last_cta;
     const int pair = blockIdx.y;
     const RunDesc& ra = p.runs[pairs[2 * pair]];
     const RunDesc& rb = p.runs[pairs[2 * pair + 1]];
@@ -43,6 +49,7 @@ __global__ void __launch_bounds__(256) k_overlap_hist(KParams p, const int32_t* 
     const int li = threadIdx.x % G;
     const int Wq = ra.Wp >> 2;  // 128-bit words per row
     uint32_t* out = hist + (size_t)pair * bins;
+    uint32_t* acc = acc_all + (size_t)pair * bins;  // zero between calls
     if (SMEM_HIST) {
         for (int k = threadIdx.x; k < bins; k += blockDim.x) sh[k] = 0u;
         __syncthreads();
@@ -66,13 +73,24 @@ __global__ void __launch_bounds__(256) k_overlap_hist(KParams p, const int32_t* 
         for (int o = G >> 1; o > 0; o >>= 1) k += __shfl_down_sync(0xffffffffu, k, o, G);
         if (li == 0 && j < n) {
             if (SMEM_HIST) atomicAdd(&sh[k], 1u);
-            else atomicAdd(&out[k], 1u);
+            else atomicAdd(&acc[k], 1u);
         }
     }
     if (SMEM_HIST) {
         __syncthreads();
         for (int k = threadIdx.x; k < bins; k += blockDim.x)
-            if (sh[k]) atomicAdd(&out[k], sh[k]);
+            if (sh[k]) atomicAdd(&acc[k], sh[k]);
+    }
+    // make this CTA's additions visible, then take a ticket; the last CTA of the
+    // pair sees every other CTA's additions
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last_cta = (atomicAdd(&tickets[pair], 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (last_cta) {
+        __threadfence();
+        for (int k = threadIdx.x; k < bins; k += blockDim.x) out[k] = atomicExch(&acc[k], 0u);
+        if (threadIdx.x == 0) tickets[pair] = 0u;
     }
 }
 
@@ -112,14 +130,12 @@ int overlap_lanes(int Wp) {
 
 cudaError_t launch_overlap(const KParams& p, const int32_t* pairs, int n_pairs, int Wp,
                            uint32_t max_rows, int bins, uint32_t* hist, double* P,
-                           cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n_pairs * bins, s);
-    if (e != cudaSuccess) return e;
+                           uint32_t* acc, uint32_t* tickets, cudaStream_t s) {
     const int G = overlap_lanes(Wp);
     // CTAs per pair: about eight CTAs per SM over all pairs, each looping over
     // its share of the replica pairs
     int dev = 0, nsm = 0;
-    e = cudaGetDevice(&dev);
+    cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const uint64_t passes = ((uint64_t)max_rows * G + 255) / 256;
@@ -127,9 +143,10 @@ cudaError_t launch_overlap(const KParams& p, const int32_t* pairs, int n_pairs, 
     const int per_pair = (int)std::max<uint64_t>(1, std::min<uint64_t>(passes, want));
     const dim3 grid((unsigned)per_pair, (unsigned)n_pairs);
     if (bins <= 12288)
-        k_overlap_hist<true><<<grid, 256, (size_t)bins * 4, s>>>(p, pairs, G, bins, hist);
+        k_overlap_hist<true><<<grid, 256, (size_t)bins * 4, s>>>(p, pairs, G, bins, hist, acc,
+                                                                 tickets);
     else
-        k_overlap_hist<false><<<grid, 256, 0, s>>>(p, pairs, G, bins, hist);
+        k_overlap_hist<false><<<grid, 256, 0, s>>>(p, pairs, G, bins, hist, acc, tickets);
     e = cudaGetLastError();
     if (e != cudaSuccess || !P) return e;
     k_overlap_P<<<(bins + 127) / 128, 128, 0, s>>>(p, pairs, n_pairs, bins, hist, P);

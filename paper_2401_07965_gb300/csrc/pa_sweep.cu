@@ -381,7 +381,8 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
     const Geo geo = {r.L, r.N, r.magicL, r.shiftL};
     uint32_t* ms = smem;
     uint8_t* jb = reinterpret_cast<uint8_t*>(smem + r.N);
-    const int qcap = queue_capacity(r.N);
+    const int qcap = (p.qcap_limit >= 0 && p.qcap_limit < queue_capacity(r.N))
+                         ? p.qcap_limit : queue_capacity(r.N);
     uint32_t* qwords = smem + r.N + (EA ? (r.N + 15) / 16 * 4 : 0);
     __shared__ int32_t sU[32];
     __shared__ int32_t sNup[32];

@@ -35,7 +35,7 @@ EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observable
            "pa_run_trace", "pa_run_free_energy", "pa_run_get_array", "pa_weighted",
            "pa_set_graph", "pa_set_controller", "pa_schedule_taken", "pa_mlp_scratch_bytes",
            "pa_mlp_forward", "pa_mlp_gradients", "pa_mlp_adam", "pa_overlap",
-           "pa_set_partial_resampling", "pa_weighted_rows"]
+           "pa_set_partial_resampling", "pa_weighted_rows", "pa_set_sweep_queue"]
 
 
 class pa_lattice(C.Structure):
@@ -169,6 +169,7 @@ def _load():
     lib.pa_mlp_gradients.argtypes = [vp, vp, vp, vp, C.c_int32, vp, vp, vp, sz, vp]
     lib.pa_mlp_adam.argtypes = [vp, vp, vp, vp, vp, C.c_int32, C.c_float, vp]
     lib.pa_set_sweep_threads.argtypes = [vp, C.c_int32]
+    lib.pa_set_sweep_queue.argtypes = [vp, C.c_int32]
     lib.pa_get_sweep_threads.argtypes = [vp]
     lib.pa_get_sweep_threads.restype = C.c_int32
     lib.pa_strerror.argtypes = [C.c_int]
@@ -324,6 +325,10 @@ def pa_weights_static(E_ptr, R_prev, R, dim, L, parity, dbeta, lnQ_ptr, f_ptr, s
 
 def pa_set_sweep_threads(ctx, threads):
     _check(_lib.pa_set_sweep_threads(ctx, int(threads)), "pa_set_sweep_threads")
+
+
+def pa_set_sweep_queue(ctx, cap):
+    _check(_lib.pa_set_sweep_queue(ctx, int(cap)), "pa_set_sweep_queue")
 
 
 def pa_get_sweep_threads(ctx) -> int:

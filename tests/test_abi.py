@@ -81,3 +81,39 @@ def test_init_rejects_bad_schedules_without_a_gpu(lib):
     with pytest.raises(pa.PAError):
         pa.pa_init(2, 8, ("ferro",), 10, 0, np.array([0.0, 0.1, 0.2, 0.3]),
                    np.array([1, 1 << 24, 1], np.uint32), pa.PA_SYSTEMATIC, 1)
+
+
+def test_population_bound_is_refused_without_a_gpu(lib):
+    """R and R_cap must stay below 2^24: the expected copy numbers are 2^-40
+    fixed-point integers whose total R 2^40 has to fit in 64 bits."""
+    import numpy as np
+    from paper_2401_07965_gb300 import pa
+    betas, th = np.array([0.0, 0.1, 0.2]), np.ones(2, np.uint32)
+    top = (1 << 24) - 1
+    assert pa.pa_workspace_bytes(2, 4, top, 0, 2, pa.PA_SYSTEMATIC) > 0
+    assert pa.pa_workspace_bytes(2, 4, top + 1, 0, 2, pa.PA_SYSTEMATIC) == 0
+    assert pa.pa_workspace_bytes(2, 4, 1000, top + 1, 2, pa.PA_NEAREST) == 0
+    for R, cap in ((top + 1, 0), (1000, top + 1), (1 << 30, 0)):
+        with pytest.raises(pa.PAError) as ei:
+            pa.pa_init(2, 4, ("ferro",), R, cap, betas, th, pa.PA_SYSTEMATIC, 1)
+        assert ei.value.status == pa.PA_ERR_LIMIT
+        with pytest.raises(pa.PAError) as ei:
+            pa.pa_batch_init([{"dim": 2, "L": 4, "R": 10}, {"dim": 2, "L": 4, "R": R,
+                                                            "R_cap": cap}],
+                             betas, th, pa.PA_SYSTEMATIC, 1)
+        assert ei.value.status == pa.PA_ERR_LIMIT
+    # the allocation-free weights entry point checks its sizes before any CUDA call
+    with pytest.raises(pa.PAError) as ei:
+        pa.pa_weights_static(8, 4, top + 1, 2, 8, 0, 0.01, 8, 8, 0)
+    assert ei.value.status == pa.PA_ERR_LIMIT
+    with pytest.raises(pa.PAError) as ei:
+        pa.pa_weights_static(8, 4, 4, 3, 1 << 20, 0, 0.01, 8, 8, 0)
+    assert ei.value.status == pa.PA_ERR_LIMIT
+    with pytest.raises(pa.PAError) as ei:
+        pa.pa_weights_static(8, 4, 4, 2, 8, 2, 0.01, 8, 8, 0)  # parity not 0 or 1
+    assert ei.value.status == pa.PA_ERR_ARG
+
+
+def test_sweep_queue_hook_validates_arguments(lib):
+    from paper_2401_07965_gb300 import pa
+    assert pa._lib.pa_set_sweep_queue(None, 0) == pa.PA_ERR_ARG

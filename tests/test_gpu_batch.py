@@ -65,6 +65,29 @@ def test_uneven_spin_glass_batch_matches_oracle(rule):
     b.close()
 
 
+@pytest.mark.parametrize("rule", ["systematic", "nearest"])
+def test_uneven_2d_batch_matches_oracle(rule):
+    """The weighted-averaging batch shape, scaled down: 2D Ising L=32, four runs of
+    R=60 and two of R=240 (uneven populations, one ensemble), beta 0 -> 1 in 6 steps,
+    theta=3; every run spin by spin against its oracle run after every step."""
+    runs = [{"dim": 2, "L": 32, "R": 60, "ensemble": 0} for _ in range(4)]
+    runs += [{"dim": 2, "L": 32, "R": 240, "ensemble": 0} for _ in range(2)]
+    betas = np.linspace(0, 1.0, 7)
+    thetas = np.full(6, 3, np.uint32)
+    b = pa.Batch(runs, betas, thetas, rule, 2000)
+    orcs = _oracle_runs(b, 2000, rule)
+    _compare(b, orcs, "init")
+    for i in range(6):
+        b.step(1)
+        for o in orcs:
+            assert o.step() == 0
+        _compare(b, orcs, f"step {i + 1}")
+        for m, o in enumerate(orcs):
+            assert np.array_equal(b.array(m, pa.PA_ARRAY_ENERGY), o.energies()), (i, m)
+            assert np.array_equal(b.array(m, pa.PA_ARRAY_COUNTS), o.counts()), (i, m)
+    b.close()
+
+
 def test_graph_replay_equals_direct_launches():
     runs = [{"dim": 2, "L": 16, "R": 300, "ensemble": 0}, {"dim": 2, "L": 16, "R": 200,
                                                             "ensemble": 0}]

@@ -45,7 +45,11 @@ def _kaufman(L):
 
 
 @pytest.mark.parametrize("rule", RULES)
-def test_full_size_step_against_oracle(rule):
+@pytest.mark.parametrize("k", [2, 149])
+def test_full_size_step_against_oracle(rule, k):
+    """Step k+1 of the benchmark run: k = 2 (beta = 0.015, few replicas need a
+    Metropolis draw) and k = 149 (beta = 0.75, nearly every site needs one and the
+    thresholds' top bits are zero)."""
     L, R, theta, seed, n = 64, 100000, 10, 7, 200
     betas = np.linspace(0.0, 1.0, n + 1)
     thetas = np.full(n, theta, np.uint32)
@@ -57,7 +61,6 @@ def test_full_size_step_against_oracle(rule):
     rng = np.random.default_rng(1)
     for j in rng.choice(R, 16, replace=False):
         assert np.array_equal(words0[j], O.pack_spins(O.init_replica(2, L, seed, int(j))[None])[0])
-    k = 2
     g.step(k)
     E_pre, fam_pre, words_pre = g.energies(), g.families(), g.spins_words()
     g.step(1)

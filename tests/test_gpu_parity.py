@@ -55,12 +55,15 @@ def compare_step(gpu, orc, N, where, initial=False):
     assert np.array_equal(gpu.magnetisations().astype(np.int64), M), where
 
 
-def run_parity(d, L, R, nsteps, bf, theta, method, seed, kind="ferro", R_cap=0, check_every=1):
+def run_parity(d, L, R, nsteps, bf, theta, method, seed, kind="ferro", R_cap=0, check_every=1,
+               queue_cap=None):
     cpl, J = _couplings(d, L, kind)
     betas = np.linspace(0.0, bf, nsteps + 1)
     thetas = np.full(nsteps, theta, np.uint32)
     cap = R_cap or pa.default_capacity(R, method)
     gpu = pa.Population(d, L, R, betas, thetas, method, seed, couplings=cpl, R_cap=cap)
+    if queue_cap is not None:
+        pa.pa_set_sweep_queue(gpu.ctx, queue_cap)
     orc = O.Run(d, L, J, R, betas, thetas, O.RESAMPLERS[method], seed, R_cap=cap)
     N = L ** d
     compare_step(gpu, orc, N, "init", initial=True)
@@ -229,3 +232,17 @@ def test_sweep_launch_configuration_does_not_change_results(d, L, kind):
             assert cur[2] == ref[2]
     with pytest.raises(pa.PAError):
         g = pa.Population(d, L, 10, betas, th, "nearest", 6, couplings=cpl, sweep_threads=96)
+
+
+@pytest.mark.parametrize("d,L,R,kind,method,bf,caps", [
+    (2, 64, 96, "ferro", "systematic", 1.0, (0, 32)),
+    (3, 6, 150, "ea", "poisson", 3.0, (0, 4)),
+    (3, 10, 40, "ea", "nearest", 2.0, (0, 16))])
+def test_sweep_queue_overflow_path(d, L, R, kind, method, bf, caps):
+    """The sweep queues the sites still undecided after eight bits of the uniforms
+    and finishes them in a second pass; a site that finds the queue full finishes
+    at once.  With the queue capped (0: every such site finishes at once; a small
+    cap: some of each) the run must still equal the oracle bit for bit at every
+    step: 2D Ising L=64 to beta 1, 3D +-J L=6 and L=10 to beta 2-3."""
+    for cap in caps:
+        run_parity(d, L, R, 6, bf, 3, method, 29 + cap, kind=kind, queue_cap=cap)
