@@ -7,7 +7,6 @@
 // nothing.  The arithmetic is the one of the context path's weights kernel,
 // operation for operation, so both give the same bits.
 #include <cmath>
-#include <mutex>
 
 #include "../../include/pa.h"
 #include "pa_internal.cuh"
@@ -49,13 +48,14 @@ k_weights_static(StaticScratch* sc, const int32_t* __restrict__ E, uint32_t R_pr
     __threadfence_block();
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < R_prev; j += blockDim.x) {
-        const int32_t e = E[j];
-        const int32_t twoU = e + d * N;  // = 2U
-        if (twoU < 0 || twoU > 2 * d * N || (twoU & 1)) {
+        // 2U = E + dN (U unsatisfied bonds) in 64 bits: no overflow for any int32 E.
+        // A valid energy has 0 <= U <= dN and U = parity (mod 2).
+        const long long twoU = (long long)E[j] + (long long)d * N;
+        if (twoU < 0 || twoU > 2LL * d * N || (twoU & 1) || (((twoU >> 1) & 1) != parity)) {
             atomicExch(&sc->bad, 1);
             continue;
         }
-        atomicAdd(&sc->hist[(twoU >> 1) >> 1], 1u);
+        atomicAdd(&sc->hist[(int)(twoU >> 2)], 1u);
     }
     __threadfence_block();
     __syncthreads();
@@ -120,10 +120,6 @@ k_weights_static(StaticScratch* sc, const int32_t* __restrict__ E, uint32_t R_pr
     }
 }
 
-// device address of g_scratch, looked up once per device
-std::mutex g_mu;
-StaticScratch* g_addr[64] = {nullptr};
-
 }  // namespace
 
 extern "C" pa_status pa_weights_static(const int32_t* E, uint32_t R_prev, uint32_t R, int32_t dim,
@@ -133,20 +129,17 @@ extern "C" pa_status pa_weights_static(const int32_t* E, uint32_t R_prev, uint32
     if (dim < 2 || dim > 3 || L < 2 || (L & 1)) return PA_ERR_ARG;
     if (!(dbeta > 0.0) || !std::isfinite(dbeta)) return PA_ERR_ARG;
     long long N = 1;
-    for (int a = 0; a < dim; ++a) N *= L;
+    for (int a = 0; a < dim && N <= 32768; ++a) N *= L;
     if (N > 32768 || dim * N / 2 + 1 > STATIC_MAX_LEVELS) return PA_ERR_LIMIT;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PA_ERR_CUDA;
-    StaticScratch* sc = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
-            void* ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return PA_ERR_CUDA;
-            g_addr[dev] = (StaticScratch*)ptr;
-        }
-        sc = g_addr[dev];
-    }
+    if (R > pa::MAX_POPULATION) return PA_ERR_LIMIT;  // 2^40 R must fit in 64 bits
+    // The array's device address, looked up with the caller's device current on
+    // every call: a cached pointer would outlive a reset of the device's context
+    // (the module, and the array with it, is then loaded again elsewhere).  The
+    // lookup is a host-side table query; only the first one on a device loads the
+    // module.
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return PA_ERR_CUDA;
+    StaticScratch* sc = (StaticScratch*)ptr;
     const double q = std::exp(-(4.0 * dbeta));
     k_weights_static<<<1, STATIC_THREADS, 0, (cudaStream_t)cuda_stream>>>(
         sc, E, R_prev, R, dim, (int)N, parity, dbeta, q, lnQ, f);
