@@ -21,6 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "pa_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liboracle.so")
+LIB_OMP = os.path.join(BUILD_DIR, "liboracle_omp.so")  # the same source with -fopenmp
 
 MULTINOMIAL, SYSTEMATIC, RESIDUAL, POISSON, NEAREST = 0, 1, 2, 3, 4
 RESAMPLERS = {"multinomial": MULTINOMIAL, "systematic": SYSTEMATIC, "residual": RESIDUAL,
@@ -31,14 +32,17 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile pa_oracle.c into oracle/_build/liboracle.so with gcc (no FMA contraction)."""
+    """Compile pa_oracle.c with gcc (no FMA contraction) into oracle/_build/liboracle.so
+    (single thread: the parity runs) and liboracle_omp.so (-fopenmp: the replica loop of
+    the sweeps on all host cores, for the multi-core CPU baseline)."""
     os.makedirs(BUILD_DIR, exist_ok=True)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=gnu99", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-o", tmp, SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
+    for out, extra in ((LIB, []), (LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(SRC):
+            tmp = out + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-std=gnu99", "-fPIC", "-shared", "-ffp-contract=off",
+                   "-fno-fast-math", *extra, "-o", tmp, SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, out)
     return LIB
 
 
@@ -54,58 +58,76 @@ class Obs(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+_lib_omp = None
+
+
 def lib():
+    """The single-thread oracle library."""
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = C.CDLL(LIB)
-            u32p, u64p, i8p, i32p, dp = (C.POINTER(C.c_uint32), C.POINTER(C.c_uint64),
-                                         C.POINTER(C.c_int8), C.POINTER(C.c_int32),
-                                         C.POINTER(C.c_double))
-            L.or_philox.argtypes = [u32p, u32p, u32p]
-            L.or_exp.argtypes = [C.c_double]
-            L.or_exp.restype = C.c_double
-            L.or_energy.argtypes = [C.c_int, C.c_int, i8p, i8p]
-            L.or_energy.restype = C.c_int32
-            L.or_disorder.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32, i8p]
-            L.or_init_replica.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32, i8p]
-            L.or_thresholds.argtypes = [C.c_double, u32p]
-            L.or_sweeps.argtypes = [C.c_int, C.c_int, i8p, i8p, i32p, C.c_uint64, C.c_uint32,
-                                    C.c_uint32, C.c_uint32, u32p]
-            L.or_sweeps.restype = C.c_uint64
-            L.or_u_less.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int,
-                                    C.c_int, C.c_uint32]
-            L.or_u_less.restype = C.c_int
-            L.or_resample.argtypes = [i32p, C.c_uint32, C.c_uint32, C.c_double, C.c_int,
-                                      C.c_uint64, C.c_uint32, C.c_uint32, u32p, u64p, dp, u64p]
-            L.or_resample.restype = C.c_int
-            L.or_run_create.argtypes = [C.c_int, C.c_int, i8p, C.c_uint32, C.c_uint32, C.c_int,
-                                        dp, u32p, C.c_int, C.c_uint64]
-            L.or_run_create.restype = C.c_void_p
-            L.or_run_create_ex.argtypes = [C.c_int, C.c_int, i8p, C.c_uint32, C.c_uint32,
-                                           C.c_int, dp, u32p, C.c_int, C.c_uint64, C.c_uint32,
-                                           C.c_uint32]
-            L.or_run_create_ex.restype = C.c_void_p
-            L.or_run_destroy.argtypes = [C.c_void_p]
-            L.or_run_step.argtypes = [C.c_void_p]
-            L.or_run_step.restype = C.c_int
-            for name, rt in [("or_run_status", C.c_int), ("or_run_step_index", C.c_int),
-                             ("or_run_size", C.c_uint32), ("or_run_prev_size", C.c_uint32),
-                             ("or_run_sum_lnQ", C.c_double), ("or_run_minus_beta_F", C.c_double),
-                             ("or_run_spins", C.c_void_p), ("or_run_energies", C.c_void_p),
-                             ("or_run_families", C.c_void_p), ("or_run_counts", C.c_void_p),
-                             ("or_run_fixed_weights", C.c_void_p),
-                             ("or_run_ancestors", C.c_void_p),
-                             ("or_run_weights", C.c_void_p)]:
-                f = getattr(L, name)
-                f.argtypes = [C.c_void_p]
-                f.restype = rt
-            L.or_run_obs.argtypes = [C.c_void_p, C.POINTER(Obs)]
-            L.or_run_set_partial.argtypes = [C.c_void_p, C.c_double]
-            L.or_run_set_partial.restype = C.c_int
-            _lib = L
+            _lib = _declare(C.CDLL(LIB))
     return _lib
+
+
+def lib_omp():
+    """The same oracle built with -fopenmp (replica loop of the sweeps on all cores)."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            build()
+            _lib_omp = _declare(C.CDLL(LIB_OMP))
+    return _lib_omp
+
+
+def _declare(L):
+    """Argument and result types of the oracle's C entry points."""
+    u32p, u64p, i8p, i32p, dp = (C.POINTER(C.c_uint32), C.POINTER(C.c_uint64),
+                                 C.POINTER(C.c_int8), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_double))
+    L.or_philox.argtypes = [u32p, u32p, u32p]
+    L.or_exp.argtypes = [C.c_double]
+    L.or_exp.restype = C.c_double
+    L.or_energy.argtypes = [C.c_int, C.c_int, i8p, i8p]
+    L.or_energy.restype = C.c_int32
+    L.or_disorder.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32, i8p]
+    L.or_init_replica.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32, i8p]
+    L.or_thresholds.argtypes = [C.c_double, u32p]
+    L.or_sweeps.argtypes = [C.c_int, C.c_int, i8p, i8p, i32p, C.c_uint64, C.c_uint32,
+                            C.c_uint32, C.c_uint32, u32p]
+    L.or_sweeps.restype = C.c_uint64
+    L.or_u_less.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int,
+                            C.c_int, C.c_uint32]
+    L.or_u_less.restype = C.c_int
+    L.or_resample.argtypes = [i32p, C.c_uint32, C.c_uint32, C.c_double, C.c_int,
+                              C.c_uint64, C.c_uint32, C.c_uint32, u32p, u64p, dp, u64p]
+    L.or_resample.restype = C.c_int
+    L.or_run_create.argtypes = [C.c_int, C.c_int, i8p, C.c_uint32, C.c_uint32, C.c_int,
+                                dp, u32p, C.c_int, C.c_uint64]
+    L.or_run_create.restype = C.c_void_p
+    L.or_run_create_ex.argtypes = [C.c_int, C.c_int, i8p, C.c_uint32, C.c_uint32,
+                                   C.c_int, dp, u32p, C.c_int, C.c_uint64, C.c_uint32,
+                                   C.c_uint32]
+    L.or_run_create_ex.restype = C.c_void_p
+    L.or_run_destroy.argtypes = [C.c_void_p]
+    L.or_run_step.argtypes = [C.c_void_p]
+    L.or_run_step.restype = C.c_int
+    for name, rt in [("or_run_status", C.c_int), ("or_run_step_index", C.c_int),
+                     ("or_run_size", C.c_uint32), ("or_run_prev_size", C.c_uint32),
+                     ("or_run_sum_lnQ", C.c_double), ("or_run_minus_beta_F", C.c_double),
+                     ("or_run_spins", C.c_void_p), ("or_run_energies", C.c_void_p),
+                     ("or_run_families", C.c_void_p), ("or_run_counts", C.c_void_p),
+                     ("or_run_fixed_weights", C.c_void_p),
+                     ("or_run_ancestors", C.c_void_p),
+                     ("or_run_weights", C.c_void_p)]:
+        f = getattr(L, name)
+        f.argtypes = [C.c_void_p]
+        f.restype = rt
+    L.or_run_obs.argtypes = [C.c_void_p, C.POINTER(Obs)]
+    L.or_run_set_partial.argtypes = [C.c_void_p, C.c_double]
+    L.or_run_set_partial.restype = C.c_int
+    return L
 
 
 def _p(a, ct):
@@ -187,42 +209,45 @@ class Run:
     """A whole PA run of the oracle: Run(...).step() advances one temperature step."""
 
     def __init__(self, d, L, J, R, betas, thetas, method, seed, R_cap=0, slot_base=0, run_id=0,
-                 alpha=None):
+                 alpha=None, parallel=False):
+        """parallel=True runs the replica loop of the sweeps on all host cores (OpenMP
+        build, OMP_NUM_THREADS threads); the results are the same."""
+        self._L = lib_omp() if parallel else lib()
         self.d, self.L, self.N = d, L, L ** d
         self.J = np.ascontiguousarray(J, np.int8)
         self.betas = np.ascontiguousarray(betas, np.float64)
         self.thetas = np.ascontiguousarray(thetas, np.uint32)
-        self._h = lib().or_run_create_ex(d, L, _p(self.J, C.c_int8), R, R_cap,
+        self._h = self._L.or_run_create_ex(d, L, _p(self.J, C.c_int8), R, R_cap,
                                          len(self.betas) - 1, _p(self.betas, C.c_double),
                                          _p(self.thetas, C.c_uint32), int(method), seed,
                                          slot_base, run_id)
         if not self._h:
             raise ValueError("oracle: invalid run arguments")
         self.R = R
-        if alpha is not None and lib().or_run_set_partial(self._h, float(alpha)) != 0:
+        if alpha is not None and self._L.or_run_set_partial(self._h, float(alpha)) != 0:
             raise ValueError("oracle: invalid partial-resampling threshold")
         self.partial = alpha is not None
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().or_run_destroy(h)
+            self._L.or_run_destroy(h)
             self._h = None
 
     def step(self) -> int:
-        return lib().or_run_step(self._h)
+        return self._L.or_run_step(self._h)
 
     @property
     def status(self):
-        return lib().or_run_status(self._h)
+        return self._L.or_run_status(self._h)
 
     @property
     def size(self) -> int:
-        return lib().or_run_size(self._h)
+        return self._L.or_run_size(self._h)
 
     @property
     def prev_size(self) -> int:
-        return lib().or_run_prev_size(self._h)
+        return self._L.or_run_prev_size(self._h)
 
     def _arr(self, fn, ct, n, dt):
         ptr = getattr(lib(), fn)(self._h)
@@ -255,14 +280,14 @@ class Run:
 
     def obs(self) -> dict:
         o = Obs()
-        lib().or_run_obs(self._h, C.byref(o))
+        self._L.or_run_obs(self._h, C.byref(o))
         return o.as_dict()
 
     def sum_lnQ(self) -> float:
-        return lib().or_run_sum_lnQ(self._h)
+        return self._L.or_run_sum_lnQ(self._h)
 
     def minus_beta_F(self) -> float:
-        return lib().or_run_minus_beta_F(self._h)
+        return self._L.or_run_minus_beta_F(self._h)
 
 
 def pack_spins(sig: np.ndarray) -> np.ndarray:

@@ -810,11 +810,17 @@ int or_run_step(or_run *r)
     r->Rprev = Rprev;
     r->Rcur = (uint32_t)Rnew;
     r->sum_lnQ += lnQ;
-    /* step 3: theta_i sweeps at beta_i */
+    /* step 3: theta_i sweeps at beta_i.  The replicas are independent single-
+     * replica chains; built with -fopenmp (the multi-core CPU baseline) the loop
+     * is shared among the host cores, with the same result. */
     or_thresholds(r->beta[i], thr);
-    for (j = 0; j < r->Rcur; ++j)
-        acc += or_sweeps(r->d, r->L, r->J, r->sig + (size_t)j * N, &r->E[j], r->seed,
-                         (uint32_t)i, r->slot_base + j, r->theta[i - 1], thr);
+    {
+        long jj, nrep = (long)r->Rcur;
+#pragma omp parallel for reduction(+ : acc) schedule(static)
+        for (jj = 0; jj < nrep; ++jj)
+            acc += or_sweeps(r->d, r->L, r->J, r->sig + (size_t)jj * N, &r->E[jj], r->seed,
+                             (uint32_t)i, r->slot_base + (uint32_t)jj, r->theta[i - 1], thr);
+    }
     r->step = i;
     /* step 4: measure */
     measure(r, r->counts, r->f_rep, Rprev, lnQ, acc);

@@ -123,3 +123,18 @@ def test_checkpoint_free_determinism(oracle):
     for _ in range(5):
         a.step(); b.step()
     assert np.array_equal(a.spins(), b.spins()) and a.obs() == b.obs()
+
+
+def test_openmp_build_gives_the_same_run(oracle):
+    """The multi-core build (replica loop of the sweeps shared among host cores)
+    reproduces the single-thread run bit for bit."""
+    J = oracle.disorder(3, 4, 3, 1)
+    betas = np.linspace(0.0, 2.0, 7)
+    th = np.full(6, 3, np.uint32)
+    a = oracle.Run(3, 4, J, 300, betas, th, oracle.POISSON, 8, R_cap=600)
+    b = oracle.Run(3, 4, J, 300, betas, th, oracle.POISSON, 8, R_cap=600, parallel=True)
+    for _ in range(6):
+        assert a.step() == 0 and b.step() == 0
+        assert np.array_equal(a.spins(), b.spins())
+        assert np.array_equal(a.families(), b.families())
+        assert a.obs() == b.obs()
