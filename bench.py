@@ -43,26 +43,37 @@ RULES = ["multinomial", "systematic", "residual", "poisson", "nearest"]
 L, DIM, R, NSTEPS, THETA, SEED, BETA_F = 64, 2, 100_000, 200, 10, 7, 1.0
 WORKLOAD = ("2D Ising ferromagnet L=64 periodic, R=100000, beta 0->1 in 200 steps, theta=10, "
             "multinomial/systematic/residual/Poisson/nearest-integer runs, seed 7")
-# Roofline of the sweep kernel (integer ALU bound).  Per site word (one site of
-# the 32 replicas of a CTA) the bit-plane Metropolis test needs, with an ideal
+# Roofline of the sweep kernel (integer pipes).  Per site word (one site of the
+# 32 replicas of a CTA) the bit-plane Metropolis test needs, with an ideal
 # per-site stop at the first deciding plane block, E_B Philox blocks, where
 # E_B = sum_g P(some replica undecided after 4g planes) = sum_g 1-(1-16^-g)^32.
 # Per block: 14 wide multiplies (rounds 4-10; rounds 1-3 are shared by the
-# counter layout) and 17 ALU operations (their 14 three-input XORs and 3 to
-# combine the shared halves), plus 4 ALU operations per plane (threshold bits of
-# the replica classes: 2; the borrow and the "equal so far" update: 1 each) for
-# d = 2.
-# Per site: 2 wide multiplies (rounds 2-3) and 12 ALU operations (four
-# neighbour XORs, the class masks, the flip).  ALU operations run on a pipe of
-# 64 lanes per clock per SM (ncu: sm__inst_executed_pipe_alu peak = 2 warp
-# instructions per cycle); wide multiplies on one of 32 per clock (probe).
+# counter layout) and 17 logic operations (their 14 three-input XORs and 3 to
+# combine the shared halves); per plane, for d = 2, the replicas' threshold bit
+# word as c4 b4 + c8 b8 (the two classes' masks are disjoint, bits 0/1: one
+# multiply and one multiply-add) and 2 logic operations (the borrow and the
+# "equal so far" words).  Per site: 2 wide multiplies (rounds 2-3) and 12 logic
+# operations (four neighbour XORs, the class masks, the flip).
+# Pipes per SM and clock: the integer ALU pipe takes 64 lane-operations (ncu:
+# sm__inst_executed_pipe_alu peak = 2 warp instructions per cycle), the
+# multiply (FMA-heavy) pipe 64 lane-operations with a 32x32->64 product taking
+# two of them (a probe measured 25-28 products per clock per SM), and the
+# schedulers issue 4 warp instructions (128 lane-instructions).  The roofline is
+# set by the most loaded of the three.
 E_BLOCKS = sum(1.0 - (1.0 - 16.0 ** -g) ** 32 for g in range(8))
-ALU_OPS_PER_SITEWORD = 12 + E_BLOCKS * (17 + 4 * 4)
+ALU_OPS_PER_SITEWORD = 12 + E_BLOCKS * (17 + 4 * 2)
 MULWIDE_PER_SITEWORD = 2 + E_BLOCKS * 14
-ALU_OPS_PER_UPDATE = ALU_OPS_PER_SITEWORD / 32.0
-MULWIDE_PER_UPDATE = MULWIDE_PER_SITEWORD / 32.0
+IMAD_PER_SITEWORD = E_BLOCKS * 4 * 2
+FMA_CYCLES_PER_SITEWORD = 2 * MULWIDE_PER_SITEWORD + IMAD_PER_SITEWORD
+ISSUE_PER_SITEWORD = ALU_OPS_PER_SITEWORD + MULWIDE_PER_SITEWORD + IMAD_PER_SITEWORD
 ALU_LANES_PER_SM = 64
-MULWIDE_PER_SM = 32
+FMA_LANES_PER_SM = 64
+ISSUE_LANES_PER_SM = 128
+PIPES = {"alu": (ALU_OPS_PER_SITEWORD, ALU_LANES_PER_SM),
+         "fma": (FMA_CYCLES_PER_SITEWORD, FMA_LANES_PER_SM),
+         "issue": (ISSUE_PER_SITEWORD, ISSUE_LANES_PER_SM)}
+BINDING_PIPE = max(PIPES, key=lambda k: PIPES[k][0] / PIPES[k][1])
+ALU_OPS_PER_UPDATE = ALU_OPS_PER_SITEWORD / 32.0
 
 
 def _env_rank():
@@ -149,7 +160,7 @@ def _sweep_traffic(kernel_src_hash):
 
 def _src_hash():
     h = hashlib.sha256()
-    for f in ("pa_sweep.cu", "pa_internal.cuh"):
+    for f in ("pa_sweep2d.cu", "pa_sweep_common.cuh", "pa_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2401_07965_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -366,22 +377,24 @@ def run_ours(args):
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     clocks = clk.summary()
     f_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak_alu = nsm * ALU_LANES_PER_SM * f_hz / 1e12           # T ALU ops / s
-    peak_mul = nsm * MULWIDE_PER_SM * f_hz / 1e12             # T wide multiplies / s
     sweep_rate = sweep_upd / (sweep_ms * 1e6)  # updates / ns inside the sweep kernel
-    achieved = ALU_OPS_PER_UPDATE * sweep_rate * 1e9 / 1e12
+    per_sw, lanes = PIPES[BINDING_PIPE]
+    peak = nsm * lanes * f_hz / 1e12                       # T lane-operations / s
+    achieved = per_sw / 32.0 * sweep_rate * 1e9 / 1e12
     traffic_full = _sweep_traffic(_src_hash())
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "Tops/s",
-            "frac": achieved / peak_alu, "traffic": traffic_full,
-            "kernel": "k_group<2,false,T> (gather + theta bit-plane Metropolis sweeps + measure)",
-            "peak_source": f"{nsm} SMs x {ALU_LANES_PER_SM} ALU-pipe lanes x sm_max_mhz "
-                           f"({peak_src} clocks); ALU-pipe lanes from ncu's pipe peak",
-            "alu_ops_per_update": ALU_OPS_PER_UPDATE,
-            "mulwide_per_update": MULWIDE_PER_UPDATE,
-            "mulwide_frac": MULWIDE_PER_UPDATE * sweep_rate * 1e9 / 1e12 / peak_mul,
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-ops/s",
+            "frac": achieved / peak, "traffic": traffic_full,
+            "kernel": "k_sweep2d<64,T,false> (gather + theta bit-plane Metropolis sweeps + "
+                      "measure)",
+            "binding_pipe": BINDING_PIPE,
+            "peak_source": f"{nsm} SMs x {lanes} lanes of the {BINDING_PIPE} pipe x sm_max_mhz "
+                           f"({peak_src} clocks); lanes per pipe from ncu's pipe peaks",
+            "per_site_word": {k: v[0] for k, v in PIPES.items()},
+            "pipe_fracs": {k: v[0] / 32.0 * sweep_rate * 1e9 / (nsm * v[1] * f_hz)
+                           for k, v in PIPES.items()},
             "sweep_updates_per_ns": sweep_rate,
             "sweep_launches_timed": sweep_n,
-            "roofline_updates_per_ns": peak_alu * 1e3 / ALU_OPS_PER_UPDATE,
+            "roofline_updates_per_ns": peak * 1e3 * 32.0 / per_sw,
             "sweep_share_of_step_time": sweep_ms / total_ms if world == 1 else None}
     cpu = cpu_mt = None
     if not args.no_cpu_baseline and world == 1:
@@ -409,20 +422,21 @@ def run_ours(args):
 
 
 def run_small(args):
-    """Profiling case: one run of R=20000 replicas of the benchmark lattice, systematic
-    rule; W warm-up steps then K steps, all on one context."""
+    """Profiling case: one run of --replicas replicas (default 20000) of the benchmark
+    lattice, systematic rule; W warm-up steps then K steps, all on one context."""
     import torch
     from paper_2401_07965_gb300 import pa
     betas = np.linspace(0.0, BETA_F, NSTEPS + 1)
     thetas = np.full(NSTEPS, THETA, np.uint32)
     stream = torch.cuda.current_stream()
-    p = pa.Population(DIM, L, 20000, betas, thetas, "systematic", SEED, stream=stream,
+    p = pa.Population(DIM, L, args.replicas, betas, thetas, "systematic", SEED, stream=stream,
                       sweep_threads=args.threads)
     p.step(args.warmup)
     pa.pa_enable_timing(p.ctx, True)
     p.step(args.steps)
     ms, n, u = pa.pa_sweep_timing(p.ctx)
-    print(json.dumps({"case": "small", "R": 20000, "threads": pa.pa_get_sweep_threads(p.ctx),
+    print(json.dumps({"case": "small", "R": args.replicas,
+                      "threads": pa.pa_get_sweep_threads(p.ctx),
                       "sweep_ms_per_launch": ms / max(n, 1),
                       "sweep_updates_per_ns": u / (ms * 1e6)}), flush=True)
     p.close()
@@ -900,6 +914,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the time-to-1e-4 sub-record of the headline line")
     ap.add_argument("--threads", type=int, default=0, help="small case: sweep threads per CTA")
+    ap.add_argument("--replicas", type=int, default=20000, help="small case: population size")
     ap.add_argument("--seeds", type=int, default=24, help="controller workload: seeds per arm")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: one run of R=20000 replicas of the same lattice (profiling)")

@@ -541,6 +541,9 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     p.ctl = nullptr;
     p.alpha = -1.0;
     p.qcap_limit = -1;
+    p.L_all = ctx->runs[0].L;
+    for (const RunHost& h : ctx->runs)
+        if (h.L != p.L_all) p.L_all = 0;
     ctx->d_ctl = (CtlDev*)(base + lay.shared_off[S_CTL]);
     ctx->d_gbeta = (double*)(base + lay.shared_off[S_GBETA]);
     ctx->d_gthr = (uint32_t*)(base + lay.shared_off[S_GTHR]);

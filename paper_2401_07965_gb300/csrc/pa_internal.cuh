@@ -194,6 +194,7 @@ struct KParams {
     const CtlDev* ctl;       // null without a controller
     double alpha;            // partial resampling threshold (< 0: resample every step)
     int qcap_limit;          // sweep: cap on the undecided-site queue (< 0: its full size)
+    int L_all;               // the side L shared by every run of the batch (0 if they differ)
 };
 
 // partial resampling: blocks of a run whose tree sums one CTA can finish
@@ -215,6 +216,8 @@ cudaError_t launch_partial_init(const KParams& p, cudaStream_t s);
 cudaError_t launch_sweep(const KParams& p, int threads, cudaStream_t s);
 cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int64_t* launches);
 cudaError_t prepare_sweep(const KParams& p, int threads);
+cudaError_t launch_sweep2d(const KParams& p, int threads, cudaStream_t s, bool attr_only,
+                           bool* done);
 cudaError_t launch_control(const KParams& p, cudaStream_t s);
 int sweep_threads(int N);
 bool sweep_threads_supported(int t);
