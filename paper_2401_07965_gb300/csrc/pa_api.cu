@@ -36,7 +36,8 @@ struct RunHost {
 
 enum Region {
     R_SPIN0, R_SPIN1, R_E0, R_E1, R_F0, R_F1, R_M, R_ANC, R_CNT, R_C, R_G, R_HIST, R_FLEV, R_TREE,
-    R_PA, R_PB, R_OA, R_OB, R_PD, R_PCL, R_W, R_WP, R_OP, R_JB, R_ST, R_TRACE, R_COUNT
+    R_PA, R_PB, R_OA, R_OB, R_PD, R_PCL, R_W, R_WP, R_OP, R_JB, R_ST, R_TRACE, R_LB1, R_LB2,
+    R_TICK, R_COUNT
 };
 
 enum Shared {
@@ -202,6 +203,8 @@ Layout make_layout(const std::vector<RunHost>& runs, int n_steps) {
         rs[R_JB] = (size_t)h.N;
         rs[R_ST] = sizeof(DevState);
         rs[R_TRACE] = (size_t)(n_steps + 1) * sizeof(TraceRow);
+        rs[R_LB1] = rs[R_LB2] = (size_t)h.nblk * sizeof(LBDesc);
+        rs[R_TICK] = 2 * sizeof(uint32_t);
         for (int r = 0; r < R_COUNT; ++r) {
             off[r] = o;
             o += align256(rs[r]);
@@ -279,6 +282,14 @@ pa_status map_dev_status(int s) {
             return PA_ERR_CUDA;        \
         }                              \
     } while (0)
+
+// look-back descriptors and block tickets start at zero (epoch 0 tags nothing)
+cudaError_t clear_lookback(const RunDesc& r, const RunHost& h, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(r.lb1, 0, (size_t)h.nblk * sizeof(LBDesc), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r.lb2, 0, (size_t)h.nblk * sizeof(LBDesc), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r.tick, 0, 2 * sizeof(uint32_t), s);
+    return e;
+}
 
 pa_status read_state(pa_ctx* ctx, int run, DevState* st) {
     PA_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -605,6 +616,9 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
         r.jbits = (const uint8_t*)(base + off[R_JB]);
         r.st = (DevState*)(base + off[R_ST]);
         r.trace = (TraceRow*)(base + off[R_TRACE]);
+        r.lb1 = (LBDesc*)(base + off[R_LB1]);
+        r.lb2 = (LBDesc*)(base + off[R_LB2]);
+        r.tick = (uint32_t*)(base + off[R_TICK]);
     }
     p.nblk_total = blk0;
     p.ngrp_total = grp0;
@@ -645,6 +659,7 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
             e = cudaMemsetAsync(r.trace, 0, (size_t)(n + 1) * sizeof(TraceRow), ctx->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(r.counts, 0, (size_t)h.Rcap * 4, ctx->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(r.anc, 0, (size_t)h.Rcap * 4, ctx->stream);
+        if (e == cudaSuccess) e = clear_lookback(r, h, ctx->stream);
     }
     if (e == cudaSuccess)
         e = cudaMemsetAsync(ctx->d_ovacc, 0, (size_t)M * (maxN + 1) * 4, ctx->stream);
@@ -891,6 +906,8 @@ pa_status pa_set_state(pa_ctx* ctx, const uint32_t* spins, const uint32_t* famil
     st.sum_lnQ = sum_lnQ;
     PA_CUDA(cudaMemcpy(r.st, &st, sizeof(st), cudaMemcpyHostToDevice));
     PA_CUDA(cudaMemset(r.hist, 0, (size_t)h.nlev * 4));
+    PA_CUDA(clear_lookback(r, h, ctx->stream));
+    PA_CUDA(cudaStreamSynchronize(ctx->stream));
     TraceRow t;
     std::memset(&t, 0, sizeof(t));
     t.sum_lnQ = sum_lnQ;

@@ -114,6 +114,19 @@ struct DevState {
     int32_t resample;  // partial resampling: this step resamples
     int32_t wexp;      // partial resampling: exponent of the largest new weight
     double S_new;      // partial resampling: sum of the new weights
+    uint32_t epoch;    // resampling steps taken (tags the look-back descriptors)
+    int32_t kmax;      // a Poisson inversion of this step hit its limit
+};
+
+// Look-back descriptor of one scan block (single-pass scans of the resampling
+// step): the block's aggregate, then its inclusive prefix, published with a
+// flag tagged by the step's epoch (2e+1: aggregate, 2e+2: inclusive prefix).
+struct LBDesc {
+    uint32_t flag;
+    uint32_t pad;
+    unsigned long long agg[2];
+    unsigned long long inc[2];
+    unsigned long long pad2;
 };
 
 // Per-step accumulators, device-resident (row i = after temperature step i).
@@ -168,6 +181,9 @@ struct RunDesc {
     const uint8_t* jbits;    // bit a of byte s: bond (s, s+e_a) has J = -1
     DevState* st;
     TraceRow* trace;         // n_steps + 1 rows
+    LBDesc* lb1;             // look-back descriptors: prefix of the expected copies
+    LBDesc* lb2;             // and of the copy numbers
+    uint32_t* tick;          // [0] scan-block tickets, [1] family-block tickets
 };
 
 // Batch-wide parameters, passed by value to every kernel.

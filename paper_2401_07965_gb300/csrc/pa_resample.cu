@@ -229,15 +229,38 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
     }
     const double S = t[0];
     const double Rd = (double)r.R;
+    // f_k, and the totals T = sum_j f_j = sum_k n_k f_k and of the fractional parts
+    // (exact integer sums; the copy-count kernels need them before any scan)
+    unsigned long long sT = 0, sTr = 0;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         double a = __dmul_rn(Rd, pow_bin(q, (uint32_t)k));
         a = __ddiv_rn(a, S);
         a = scalbn(a, FRAC_BITS);
-        r.flev[k] = (uint64_t)floor(a);
+        const uint64_t f = (uint64_t)floor(a);
+        r.flev[k] = f;
+        const uint64_t n = r.hist[lmin + k];
+        sT += n * f;
+        sTr += n * (f & ((1ull << FRAC_BITS) - 1));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sT += __shfl_xor_sync(0xffffffffu, sT, o);
+        sTr += __shfl_xor_sync(0xffffffffu, sTr, o);
+    }
+    __shared__ unsigned long long tsum[2];
+    if (threadIdx.x == 0) tsum[0] = tsum[1] = 0ull;
+    __syncthreads();
+    if (lane == 0) {
+        atomicAdd(&tsum[0], sT);
+        atomicAdd(&tsum[1], sTr);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) r.hist[lmin + k] = 0u;
     if (threadIdx.x == 0) {
+        st->T = tsum[0];
+        st->Tres = tsum[1];
+        st->Rres = (uint64_t)r.R - ((tsum[0] - tsum[1]) >> FRAC_BITS);
+        st->epoch += 1u;
+        st->kmax = 0;
         const int32_t Umin = 2 * lmin + r.parity;
         const int32_t Emin = 2 * Umin - p.d * r.N;
         const double lnQ = __dsub_rn(__dsub_rn(log(S), log((double)Rprev)),
@@ -661,13 +684,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scatter(KParams p) {
 // --------------------------------------------------------------------------
 // family statistics of the new population (families stay sorted by slot)
 // --------------------------------------------------------------------------
+__device__ void finish_run(const KParams& p, const RunDesc& r, DevState* st, int mode, double* a,
+                           double* b, double* ws);
+
 __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
     const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
     const uint32_t b = blockIdx.x - r.blk0;
-    const DevState* st = r.st;
+    DevState* st = r.st;
     if (st->status != S_OK) return;
-    __shared__ double sd[SCAN_THREADS];
+    __shared__ double sd[SCAN_THREADS], fa[SCAN_THREADS], fb[SCAN_THREADS];
     __shared__ unsigned long long sc2;
+    __shared__ int last;
     const int i = (mode == 0) ? st->step + 1 : st->step;
     const uint32_t Ri = st->R_cur;
     const uint32_t* fam = r.fam[i & 1];
@@ -734,20 +761,28 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
             if (threadIdx.x == 0) r.opart[5 * b + q] = root;
         }
     }
+    // the run's last family block to finish closes the step: its ticket says every
+    // other block's partials are written (each fenced them before its ticket)
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&r.tick[1], 1u) == (uint32_t)r.nblk - 1u);
+    __syncthreads();
+    if (!last) return;
+    if (threadIdx.x == 0) r.tick[1] = 0u;
+    __threadfence();
+    finish_run(p, r, st, mode, fa, fb, sd);
 }
 
-// fixed-order sums of the per-block partials, close the step
-__global__ void __launch_bounds__(256) k_finish(KParams p, int mode) {
-    const RunDesc& r = p.runs[blockIdx.x];
-    DevState* st = r.st;
-    if (st->status != S_OK) return;
-    __shared__ double a[256], b[256], ws[256];
+// fixed-order sums of the run's per-block partials, close the step (one CTA of
+// SCAN_THREADS threads; a, b, ws: shared arrays of SCAN_THREADS doubles)
+__device__ void finish_run(const KParams& p, const RunDesc& r, DevState* st, int mode, double* a,
+                           double* b, double* ws) {
     const int i = (mode == 0) ? st->step + 1 : st->step;
     const int nb_sv = (mode == 0) ? (int)((st->R_prev + SCAN_CHUNK - 1) / SCAN_CHUNK) : 0;
     const int nb_f = (int)((st->R_cur + SCAN_CHUNK - 1) / SCAN_CHUNK);
     double sa = 0.0, sb = 0.0;
-    for (int k = threadIdx.x; k < nb_sv; k += blockDim.x) sa = __dadd_rn(sa, r.partD[k]);
-    for (int k = threadIdx.x; k < nb_f; k += blockDim.x) sb = __dadd_rn(sb, r.partCL[k]);
+    for (int k = threadIdx.x; k < nb_sv; k += blockDim.x) sa = __dadd_rn(sa, __ldcg(&r.partD[k]));
+    for (int k = threadIdx.x; k < nb_f; k += blockDim.x) sb = __dadd_rn(sb, __ldcg(&r.partCL[k]));
     a[threadIdx.x] = sa;
     b[threadIdx.x] = sb;
     __syncthreads();
@@ -768,7 +803,7 @@ __global__ void __launch_bounds__(256) k_finish(KParams p, int mode) {
 #pragma unroll
             for (int k = 0; k < LEAVES; ++k) {
                 const int bb = LEAVES * threadIdx.x + k;
-                x[k] = bb < nb ? r.opart[5 * bb + q] : 0.0;
+                x[k] = bb < nb ? __ldcg(&r.opart[5 * bb + q]) : 0.0;
             }
             const double root = tree_threads(tree_regs<LEAVES>(x), ws);
             if (threadIdx.x == 0) {
@@ -789,25 +824,327 @@ __global__ void __launch_bounds__(256) k_finish(KParams p, int mode) {
 }
 
 // --------------------------------------------------------------------------
+// Single-pass scans (look-back).  A scan block takes a ticket for its logical
+// index b within its run, computes its block sums, publishes them, and obtains
+// the sum over blocks 0..b-1 from its predecessors' descriptors: the nearest
+// inclusive prefix plus the aggregates after it.  Blocks only wait on blocks
+// with earlier tickets, which are already running, so the waits end; each wait
+// is bounded all the same (a run that exceeds it reports PA_ERR_TIMEOUT).
+// --------------------------------------------------------------------------
+constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* a) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* a, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Called by the 32 lanes of warp 0.  Publishes (a0, a1) of block b and returns in
+// (p0, p1) the sums over blocks 0..b-1 (every lane); false if a wait gave up.
+__device__ bool look_back(LBDesc* d, int b, unsigned long long a0, unsigned long long a1,
+                          uint32_t ep, unsigned long long& p0, unsigned long long& p1) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t FA = 2u * ep + 1u, FI = 2u * ep + 2u;
+    if (lane == 0) {
+        d[b].agg[0] = a0;
+        d[b].agg[1] = a1;
+        if (b == 0) {
+            d[0].inc[0] = a0;
+            d[0].inc[1] = a1;
+        }
+        st_release(&d[b].flag, b == 0 ? FI : FA);
+    }
+    p0 = p1 = 0ull;
+    bool ok = true;
+    if (b > 0) {
+        int j0 = b - 1;
+        uint32_t spins = 0;
+        while (true) {
+            const int j = j0 - lane;
+            const uint32_t f = (j >= 0) ? ld_acquire(&d[j].flag) : FI;
+            const uint32_t valid = __ballot_sync(0xffffffffu, f == FA || f == FI);
+            const uint32_t incl = __ballot_sync(0xffffffffu, f == FI);
+            // lanes 0..m-1 (blocks j0, j0-1, ...) have published
+            const int m = (valid == 0xffffffffu) ? 32 : __ffs(~valid) - 1;
+            const uint32_t usable = incl & (m == 32 ? 0xffffffffu : ((1u << m) - 1u));
+            if (usable) {
+                const int k = __ffs(usable) - 1;
+                unsigned long long v0 = 0ull, v1 = 0ull;
+                if (lane < k) {
+                    v0 = __ldcg(&d[j].agg[0]);
+                    v1 = __ldcg(&d[j].agg[1]);
+                } else if (lane == k && j >= 0) {
+                    v0 = __ldcg(&d[j].inc[0]);
+                    v1 = __ldcg(&d[j].inc[1]);
+                }
+                p0 += warp_sum_u64(v0);
+                p1 += warp_sum_u64(v1);
+                break;
+            }
+            if (m == 32) {  // 32 aggregates, none inclusive: take them and look further
+                p0 += warp_sum_u64(__ldcg(&d[j].agg[0]));
+                p1 += warp_sum_u64(__ldcg(&d[j].agg[1]));
+                j0 -= 32;
+                continue;
+            }
+            if (++spins > LB_SPIN_LIMIT) {
+                ok = false;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (lane == 0 && ok) {
+            d[b].inc[0] = p0 + a0;
+            d[b].inc[1] = p1 + a1;
+            st_release(&d[b].flag, FI);
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// the block's ticket: its logical index within the run
+__device__ __forceinline__ int take_ticket(uint32_t* tick, int* sb) {
+    if (threadIdx.x == 0) *sb = (int)atomicAdd(tick, 1u);
+    __syncthreads();
+    return *sb;
+}
+
+// Copy numbers' exclusive scan (look-back over lb2), the ancestor scatter and the
+// block's sampling-variance partial; the last block sets the new population size
+// (or the capacity error) and resets the tickets.
+__device__ void count_scan_scatter(const KParams& p, const RunDesc& r, DevState* st, int b,
+                                   const uint32_t (&rc)[SCAN_ITEMS], uint64_t* sh, double* sd,
+                                   int* flag_sh) {
+    const int i = st->step + 1;
+    const int32_t* E = r.E[(i - 1) & 1];
+    const int dN = p.d * r.N;
+    const uint32_t Rprev = st->R_prev, lmin = st->lmin;
+    const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    uint64_t sum = 0;
+#pragma unroll
+    for (int e = 0; e < SCAN_ITEMS; ++e) sum += rc[e];
+    uint64_t tot;
+    const uint64_t ex = block_excl_scan(sum, sh, &tot);
+    __shared__ unsigned long long pre;
+    if (threadIdx.x < 32) {
+        unsigned long long p0, p1;
+        const bool ok = look_back(r.lb2, b, tot, 0ull, st->epoch, p0, p1);
+        if (threadIdx.x == 0) {
+            pre = p0;
+            *flag_sh = ok;
+        }
+    }
+    __syncthreads();
+    if (!*flag_sh) {
+        if (threadIdx.x == 0) atomicCAS(&st->status, S_OK, S_TIMEOUT);
+        return;
+    }
+    uint64_t o = pre + ex;
+    double sv = 0.0;
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const int j = j0 + e;
+        if ((uint32_t)j >= Rprev) break;
+        // the total is known only to the last block: slots past the capacity are
+        // not written (the last block then stops the run with the capacity error)
+        for (uint32_t c = 0; c < rc[e]; ++c)
+            if (o + c < (uint64_t)r.Rcap) r.anc[o + c] = (uint32_t)j;
+        o += rc[e];
+        const double tau = scalbn((double)f_of(j, p, r, st, dN, E, lmin), -FRAC_BITS);
+        const double dl = __dsub_rn((double)rc[e], tau);
+        sv = __dadd_rn(sv, __dmul_rn(dl, dl));
+    }
+    // fixed-order tree reduction of the block's sampling-variance terms
+    sd[threadIdx.x] = sv;
+    __syncthreads();
+    for (int h = SCAN_THREADS / 2; h >= 1; h >>= 1) {
+        if ((int)threadIdx.x < h) sd[threadIdx.x] = __dadd_rn(sd[threadIdx.x], sd[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        r.partD[b] = sd[0];
+        if (b == r.nblk - 1) {
+            const uint64_t Ri = pre + tot;
+            // a population that outgrows its capacity, or dies out, stops the run
+            if (st->kmax) st->status = S_KMAX;
+            else if (Ri > (uint64_t)r.Rcap || Ri == 0) st->status = S_CAPACITY;
+            else st->R_cur = (uint32_t)Ri;
+            r.tick[0] = 0u;
+        }
+    }
+}
+
+// Expected copies f_j, their prefix C (and that of the fractional parts, G) by
+// look-back over lb1, and the copy numbers of the rules that need no search.
+// FULL (nearest, systematic, Poisson): then the count scan and the scatter too.
+template <bool FULL>
+__global__ void __launch_bounds__(SCAN_THREADS) k_resample(KParams p) {
+    const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
+    DevState* st = r.st;
+    if (st->status != S_OK) return;
+    __shared__ uint64_t sh[33];
+    __shared__ double sd[SCAN_THREADS];
+    __shared__ int sb, okf;
+    __shared__ unsigned long long pre[2];
+    const int b = take_ticket(&r.tick[0], &sb);
+    const int i = st->step + 1;
+    const int32_t* E = r.E[(i - 1) & 1];
+    const int dN = p.d * r.N;
+    const uint32_t Rprev = st->R_prev, lmin = st->lmin;
+    const uint64_t T = st->T;
+    const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    uint64_t f[SCAN_ITEMS];
+    uint64_t sf = 0, sg = 0;
+#pragma unroll
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const int j = j0 + e;
+        f[e] = ((uint32_t)j < Rprev) ? f_of(j, p, r, st, dN, E, lmin) : 0ull;
+        sf += f[e];
+        sg += f[e] & ((1ull << FRAC_BITS) - 1);
+    }
+    uint64_t tf, tg;
+    const uint64_t ef = block_excl_scan(sf, sh, &tf);
+    const uint64_t eg = block_excl_scan(sg, sh, &tg);
+    if (threadIdx.x < 32) {
+        unsigned long long p0, p1;
+        const bool ok = look_back(r.lb1, b, tf, tg, st->epoch, p0, p1);
+        if (threadIdx.x == 0) {
+            pre[0] = p0;
+            pre[1] = p1;
+            okf = ok;
+        }
+    }
+    __syncthreads();
+    if (!okf) {
+        if (threadIdx.x == 0) atomicCAS(&st->status, S_OK, S_TIMEOUT);
+        return;
+    }
+    uint64_t cf = pre[0] + ef, cg = pre[1] + eg;
+    const int method = p.method;
+    uint32_t usys = 0;
+    if (method == M_SYSTEMATIC)
+        usys = philox(0u, DOM_RESAMPLE | (r.run << 8) | RULE_SYSTEMATIC, (uint32_t)i, 0u, p.k0, p.k1).x;
+    bool kmax = false;
+    uint32_t rc[SCAN_ITEMS];
+#pragma unroll 1
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const int j = j0 + e;
+        rc[e] = 0u;
+        if ((uint32_t)j >= Rprev) continue;
+        const uint64_t prevC = cf;
+        cf += f[e];
+        cg += f[e] & ((1ull << FRAC_BITS) - 1);
+        uint32_t cnt = 0;
+        if (method == M_NEAREST) {
+            const uint4x x = philox((uint32_t)j, DOM_RESAMPLE | (r.run << 8) | RULE_NEAREST, (uint32_t)i, 0u,
+                                    p.k0, p.k1);
+            const uint64_t u40 = (((uint64_t)x.y << 32) | x.x) >> 24;
+            cnt = (uint32_t)(f[e] >> FRAC_BITS) +
+                  (u40 < (f[e] & ((1ull << FRAC_BITS) - 1)) ? 1u : 0u);
+        } else if (method == M_SYSTEMATIC) {
+            cnt = (uint32_t)(sys_below(cf, r.R, T, usys) - sys_below(prevC, r.R, T, usys));
+        } else if (method == M_RESIDUAL) {
+            r.C[j] = cf;
+            r.G[j] = cg;
+            cnt = (uint32_t)(f[e] >> FRAC_BITS);
+        } else if (method == M_MULTINOMIAL) {
+            r.C[j] = cf;
+        } else {  // Poisson
+            const double lam = scalbn((double)f[e], -FRAC_BITS);
+            const uint32_t M = (uint32_t)(f[e] >> 44) + 1u;
+            const double lc = __ddiv_rn(lam, (double)M);
+            uint32_t total = 0;
+            for (uint32_t m = 0; m < M; ++m) {
+                const uint4x x = philox((uint32_t)j, DOM_RESAMPLE | (r.run << 8) | RULE_POISSON, (uint32_t)i, m,
+                                        p.k0, p.k1);
+                const double u = scalbn((double)((((uint64_t)x.y << 32) | x.x) >> 11), -53);
+                double pr = exp_taylor(-lc);
+                double Pc = pr;
+                uint32_t k = 0;
+                while (u >= Pc) {
+                    k += 1;
+                    if (k > POISSON_KMAX) {
+                        kmax = true;
+                        break;
+                    }
+                    pr = __ddiv_rn(__dmul_rn(pr, lc), (double)k);
+                    Pc = __dadd_rn(Pc, pr);
+                }
+                total += k;
+            }
+            cnt = total;
+        }
+        rc[e] = cnt;
+        r.counts[j] = cnt;
+    }
+    if (kmax) {  // promoted to the status word by the scan's last block
+        atomicOr(&st->kmax, 1);
+        __threadfence();
+    }
+    if (!FULL) {
+        if (threadIdx.x == 0 && b == r.nblk - 1) r.tick[0] = 0u;
+        return;
+    }
+    count_scan_scatter(p, r, st, b, rc, sh, sd, &okf);
+}
+
+// multinomial / residual: the copy numbers are complete after k_draws
+__global__ void __launch_bounds__(SCAN_THREADS) k_cscan(KParams p) {
+    const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
+    DevState* st = r.st;
+    if (st->status != S_OK) return;
+    __shared__ uint64_t sh[33];
+    __shared__ double sd[SCAN_THREADS];
+    __shared__ int sb, okf;
+    const int b = take_ticket(&r.tick[0], &sb);
+    const uint32_t Rprev = st->R_prev;
+    const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    uint32_t rc[SCAN_ITEMS];
+#pragma unroll
+    for (int e = 0; e < SCAN_ITEMS; ++e) {
+        const int j = j0 + e;
+        rc[e] = ((uint32_t)j < Rprev) ? r.counts[j] : 0u;
+    }
+    count_scan_scatter(p, r, st, b, rc, sh, sd, &okf);
+}
+
+// --------------------------------------------------------------------------
 cudaError_t launch_resample(const KParams& p, cudaStream_t s, int64_t* launches) {
     k_weights<<<p.M, 1024, 0, s>>>(p);
-    int n = 4;
+    int n = 1;
     if (p.alpha >= 0.0) {
+        // partial resampling: the expected copies depend on per-replica weights, so
+        // their total comes from a scan over the replicas
         k_pw_update<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
         k_pw_final<<<p.M, 1024, 0, s>>>(p);
-        n += 2;
-    }
-    k_fsum<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
-    k_fscan<<<p.M, 1024, 0, s>>>(p);
-    k_counts<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
-    if (p.method == M_MULTINOMIAL || p.method == M_RESIDUAL) {
+        k_fsum<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
+        k_fscan<<<p.M, 1024, 0, s>>>(p);
+        k_counts<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
+        n += 5;
+        if (p.method == M_MULTINOMIAL || p.method == M_RESIDUAL) {
+            k_draws<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
+            ++n;
+        }
+        k_rsum<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
+        k_rscan<<<p.M, 1024, 0, s>>>(p);
+        k_scatter<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
+        n += 3;
+    } else if (p.method == M_MULTINOMIAL || p.method == M_RESIDUAL) {
+        k_resample<false><<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
         k_draws<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
-        ++n;
+        k_cscan<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
+        n += 3;
+    } else {
+        k_resample<true><<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
+        n += 1;
     }
-    k_rsum<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
-    k_rscan<<<p.M, 1024, 0, s>>>(p);
-    k_scatter<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p);
-    n += 3;
     if (launches) *launches += n;
     return cudaGetLastError();
 }
@@ -819,8 +1156,7 @@ cudaError_t launch_partial_init(const KParams& p, cudaStream_t s) {
 
 cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int64_t* launches) {
     k_family<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p, mode);
-    k_finish<<<p.M, 256, 0, s>>>(p, mode);
-    if (launches) *launches += 2;
+    if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
