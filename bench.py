@@ -487,7 +487,7 @@ def run_ea3d(args):
     runs = [{"dim": 3, "L": L, "R": 50000, "couplings": ("ea", 3, 64 * k + r), "ensemble": k}
             for k, L in enumerate((4, 6, 8)) for r in range(64)]
     stream = torch.cuda.current_stream()
-    b = pa.Batch(runs, betas, thetas, "systematic", 1000, stream=stream)
+    b = pa.Batch(runs, betas, thetas, "systematic", 1000, stream=stream, sweep_threads="auto")
     K = min(args.steps, n - args.warmup)
     b.step(args.warmup)
     ms = _timed_batch(pa, b, K, stream)
@@ -515,12 +515,12 @@ def run_weighted(args):
     runs = [{"dim": 2, "L": L, "R": 2000} for _ in range(256)]
     runs += [{"dim": 2, "L": L, "R": 8000} for _ in range(64)]
     exact = _kaufman(L, 1.0)
-    b = pa.Batch(runs, betas, thetas, "systematic", 2000, stream=stream)
+    b = pa.Batch(runs, betas, thetas, "systematic", 2000, stream=stream, sweep_threads="auto")
     ms_b = _timed_batch(pa, b, n, stream)
     w = b.weighted(0)[n]
     b.close()
     s = pa.Batch([{"dim": 2, "L": L, "R": 1024000}], betas, thetas, "systematic", 3000,
-                 stream=stream)
+                 stream=stream, sweep_threads="auto")
     ms_s = _timed_batch(pa, s, n, stream)
     mbf_s, _ = s.free_energy(0)
     s.close()
@@ -549,7 +549,7 @@ def _plain_point(pa, L, n, R, thetas, seeds, stream, exact):
     betas = np.linspace(0.0, 1.0, n + 1)
     for seed in seeds:
         b = pa.Batch([{"dim": 2, "L": L, "R": R}], betas, thetas, "systematic", seed,
-                     stream=stream)
+                     stream=stream, sweep_threads="auto")
         times.append(_timed_batch(pa, b, n, stream))
         mbf, _ = b.free_energy(0)
         errs.append(abs(mbf - exact) / (L * L))
@@ -558,11 +558,28 @@ def _plain_point(pa, L, n, R, thetas, seeds, stream, exact):
             "max_err_per_spin": float(max(errs))}
 
 
+def _batch_point(pa, L, n, M, Rm, theta, seeds, stream, exact):
+    """M runs of Rm replicas in one batch (one launch per phase, graph replay), combined by
+    Eq. (weighted-averages): ln Z = ln(sum_m R_m Z_m / sum_m R_m)."""
+    errs, times = [], []
+    betas = np.linspace(0.0, 1.0, n + 1)
+    for seed in seeds:
+        b = pa.Batch([{"dim": 2, "L": L, "R": Rm, "ensemble": 0} for _ in range(M)], betas,
+                     np.full(n, theta, np.uint32), "systematic", seed, stream=stream,
+                     sweep_threads="auto")
+        times.append(_timed_batch(pa, b, n, stream))
+        w = b.weighted(0)[n]
+        errs.append(abs(w["minus_beta_F"] - exact) / (L * L))
+        b.close()
+    return {"R": Rm * M, "runs": M, "R_per_run": Rm, "steps": n, "sweeps": n * theta,
+            "ms": float(np.mean(times)), "max_err_per_spin": float(max(errs))}
+
+
 def _learned_point(pa, CT, L, K, R, budget, seeds, stream, exact, bits):
     errs, times = [], []
     for seed in seeds:
         pop = CT.controlled_run(2, L, ("ferro",), R, np.linspace(0.0, 1.0, K + 1), 4, 10, bits,
-                                seed=seed, budget=budget, stream=stream)
+                                seed=seed, budget=budget, stream=stream, sweep_threads="auto")
         times.append(_chunked(pa, pop, stream, K))
         mbf, _ = pop.free_energy()
         errs.append(abs(mbf - exact) / (L * L))
@@ -583,6 +600,8 @@ def accuracy_l64(pa, dev, seeds=(11, 12, 13, 14, 15)):
       plain:      200 equal steps, R in {3000, 10^4, 3 10^4, 10^5} x theta in {2, 5, 10};
       plain800:   800 equal steps (the learned schedule's grid) at 1000 or 2000 sweeps in
                   all, R in {3000, 10^4, 3 10^4};
+      batched:    M in {4, 8, 12} runs of 2500 replicas or 4 of 7500 in one batch, 200
+                  steps, theta in {2, 5, 10}, combined by Eq. (weighted-averages);
       learned:    the learned controller on the 800-point grid, budgets 500, 1000 or 2000
                   sweeps, R in {3000, 10^4, 3 10^4}."""
     import torch
@@ -597,8 +616,13 @@ def accuracy_l64(pa, dev, seeds=(11, 12, 13, 14, 15)):
              for R in (3000, 10000, 30000, 100000) for th in (2, 5, 10)]
     p800 = [_plain_point(pa, Lx, 800, R, _spread_thetas(800, sw), seeds, stream, exact)
             for R in (3000, 10000, 30000) for sw in (1000, 2000)]
+    batched = [_batch_point(pa, Lx, 200, M, Rm, th, seeds, stream, exact)
+               for M, Rm in ((4, 2500), (8, 2500), (12, 2500), (4, 7500)) for th in (2, 5, 10)]
     out["plain"] = {"best": _best(plain), "grid": plain}
     out["plain800"] = {"best": _best(p800), "grid": p800}
+    out["batched"] = {"best": _best(batched), "grid": batched,
+                      "what": "M runs of R/M replicas in one batch, combined by Eq. "
+                              "(weighted-averages), 200 steps"}
     if os.path.exists(CT.WEIGHTS):
         bits = CT.load()
         learned = [_learned_point(pa, CT, Lx, 800, R, bud, seeds, stream, exact, bits)
@@ -607,6 +631,7 @@ def accuracy_l64(pa, dev, seeds=(11, 12, 13, 14, 15)):
     cands = [v["best"] for k, v in out.items() if isinstance(v, dict) and v.get("best")]
     bp = [out[k]["best"] for k in ("plain", "plain800") if out[k]["best"]]
     out["best_plain_ms"] = min(g["ms"] for g in bp) if bp else None
+    out["best_batched_ms"] = out["batched"]["best"]["ms"] if out["batched"]["best"] else None
     out["best_learned_ms"] = (out["learned"]["best"]["ms"]
                               if out.get("learned", {}).get("best") else None)
     out["value_ms"] = min(g["ms"] for g in cands) if cands else None
@@ -627,6 +652,15 @@ def run_accuracy(args):
            for R in (1000, 3000, 10000, 30000) for th in (2, 5, 10)]
     acc = accuracy_l64(pa, dev)
     acc["L16"] = {"best": _best(g16), "grid": g16}
+    # the weighted-averaging lattice, L=32 with 150 steps: single runs against batches
+    exact32 = _kaufman(32, 1.0)
+    seeds = (11, 12, 13, 14, 15)
+    g32 = [_plain_point(pa, 32, 150, R, np.full(150, th, np.uint32), seeds, stream, exact32)
+           for R in (2000, 8000, 32000) for th in (2, 5, 10)]
+    b32 = [_batch_point(pa, 32, 150, M, Rm, th, seeds, stream, exact32)
+           for M, Rm in ((8, 2000), (16, 2000), (4, 8000)) for th in (2, 5)]
+    acc["L32"] = {"plain": {"best": _best(g32), "grid": g32},
+                  "batched": {"best": _best(b32), "grid": b32}}
     v = acc["value_ms"]
     _line("time to |f - f_exact| <= 1e-4 per spin at beta=1, 2D Ising L=64 (plain 200 or 800 "
           "steps, learned schedule) and L=16 (100 steps), systematic, worst of 5 seeds",
@@ -670,13 +704,14 @@ def _schedule_arm(pa, CT, sysdef, seeds, stream, plain=None, learned=None, bits=
             n, theta = plain
             pop = pa.Population(dim, L, R, np.linspace(0.0, bf, n + 1),
                                 np.full(n, theta, np.uint32), "systematic", seed,
-                                couplings=cpl, stream=stream)
+                                couplings=cpl, stream=stream, sweep_threads="auto")
             ms = _chunked(pa, pop, stream, n)
             sweeps = n * theta
         else:
             K, units, theta, budget = learned
             pop = CT.controlled_run(dim, L, cpl, R, np.linspace(0.0, bf, K + 1), units, theta,
-                                    bits, seed=seed, budget=budget, stream=stream)
+                                    bits, seed=seed, budget=budget, stream=stream,
+                                    sweep_threads="auto")
             ms = _chunked(pa, pop, stream, K)
             _, th = pa.pa_schedule_taken(pop.ctx, K + 1)
             sweeps = int(th.sum())
@@ -777,7 +812,7 @@ def run_overlap(args):
     runs = [{"dim": 2, "L": L, "R": R, "couplings": ("ea", 3, s), "ensemble": s}
             for s in range(S) for _ in range(2)]
     stream = torch.cuda.Stream()
-    b = pa.Batch(runs, betas, thetas, "systematic", 3000, stream=stream)
+    b = pa.Batch(runs, betas, thetas, "systematic", 3000, stream=stream, sweep_threads="auto")
     ms_anneal = _timed_batch(pa, b, n, stream)
     pairs = [(2 * s, 2 * s + 1) for s in range(S)]
     hist = torch.empty((S, N + 1), dtype=torch.int32, device="cuda")
@@ -842,7 +877,7 @@ def run_partial(args):
         ms, errs, res = [], [], []
         for seed in (21, 22, 23, 24, 25):
             b = pa.Batch([{"dim": 2, "L": L, "R": R}], betas, thetas, "systematic", seed,
-                         stream=stream)
+                         stream=stream, sweep_threads="auto")
             if alpha is not None:
                 b.set_partial_resampling(alpha)
             ms.append(_timed_batch(pa, b, n, stream))

@@ -72,12 +72,12 @@ def init_params(seed=0):
 
 def controlled_run(dim, L, couplings, R, betas, plain_units, plain_theta, params_bits=None,
                    seed=1, budget=0, theta_min=2, theta_max=40, u_max=8, resampler="systematic",
-                   stream=None):
+                   stream=None, sweep_threads=None):
     """A single run on the schedule grid `betas`, driven by the network (params_bits) or,
     with params_bits None, by plain steps of plain_units grid points and plain_theta sweeps."""
     n = len(betas) - 1
     pop = pa.Population(dim, L, R, betas, np.full(n, plain_theta, np.uint32), resampler, seed,
-                        couplings=couplings, stream=stream)
+                        couplings=couplings, stream=stream, sweep_threads=sweep_threads)
     pa.pa_set_controller(pop.ctx, params_bits, 0 if params_bits is None else 1, plain_units,
                          plain_theta, theta_min, theta_max, budget, u_max)
     return pop

@@ -217,23 +217,46 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
         }
         return;
     }
-    volatile double* t = r.tree;
-    for (int k = threadIdx.x; k < P; k += blockDim.x)
-        t[k] = (k < K) ? __dmul_rn((double)r.hist[lmin + k], pow_bin(q, (uint32_t)k)) : 0.0;
+    // S = sum_k n_k w_k as the fixed pairwise tree (t_k += t_{k+h}, h = P/2 ... 1) over
+    // the zero-padded array: in shared memory when it fits (the usual case: the
+    // occupied levels span a few hundred), else in the run's global scratch; the
+    // last five levels by warp shuffles with the same pairs
+    constexpr int TREE_SMEM = 2048;
+    __shared__ double tsm[TREE_SMEM], wsm[TREE_SMEM];
+    const bool in_smem = P <= TREE_SMEM;
+    volatile double* t = in_smem ? tsm : r.tree;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        double v = 0.0;
+        if (k < K) {
+            const double wk = pow_bin(q, (uint32_t)k);
+            if (in_smem) wsm[k] = wk;
+            v = __dmul_rn((double)r.hist[lmin + k], wk);
+        }
+        t[k] = v;
+    }
     __threadfence_block();
     __syncthreads();
-    for (int h = P >> 1; h >= 1; h >>= 1) {
+    int h = P >> 1;
+    for (; h >= 32; h >>= 1) {
         for (int k = threadIdx.x; k < h; k += blockDim.x) t[k] = __dadd_rn(t[k], t[k + h]);
         __threadfence_block();
         __syncthreads();
     }
-    const double S = t[0];
+    __shared__ double S_sh;
+    if (warp == 0) {
+        const int live = h > 0 ? 2 * h : 1;  // entries left after the shared-memory levels
+        double v = lane < live ? t[lane] : 0.0;
+        for (; h >= 1; h >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, h));
+        if (lane == 0) S_sh = v;
+    }
+    __syncthreads();
+    const double S = S_sh;
     const double Rd = (double)r.R;
     // f_k, and the totals T = sum_j f_j = sum_k n_k f_k and of the fractional parts
     // (exact integer sums; the copy-count kernels need them before any scan)
     unsigned long long sT = 0, sTr = 0;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        double a = __dmul_rn(Rd, pow_bin(q, (uint32_t)k));
+        double a = __dmul_rn(Rd, in_smem ? wsm[k] : pow_bin(q, (uint32_t)k));
         a = __ddiv_rn(a, S);
         a = scalbn(a, FRAC_BITS);
         const uint64_t f = (uint64_t)floor(a);

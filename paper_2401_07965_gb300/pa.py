@@ -498,6 +498,8 @@ class Population:
         self.resampler = RESAMPLERS[resampler] if isinstance(resampler, str) else int(resampler)
         self.R = R
         self.R_cap = R_cap if R_cap else default_capacity(R, self.resampler)
+        self._spec = {"dim": dim, "L": L, "R": R, "R_cap": R_cap, "couplings": couplings}
+        self._stream_obj = stream
         self._ws = None
         ws_ptr, ws_bytes, stream_ptr = 0, 0, 0
         if use_torch_memory:
@@ -514,8 +516,16 @@ class Population:
             stream_ptr = stream.cuda_stream
         self.ctx = pa_init(dim, L, couplings, R, R_cap, self.betas, self.thetas, self.resampler,
                            seed, stream_ptr, ws_ptr, ws_bytes)
+        if sweep_threads == "auto":  # the autotuner's choice for this shape (cached)
+            from . import tune
+            sweep_threads = tune.best_sweep_threads_batch(
+                self._tune_specs(), theta=int(np.median(self.thetas)) if len(self.thetas) else 0,
+                stream=getattr(self, "_stream_obj", None))
         if sweep_threads:
             pa_set_sweep_threads(self.ctx, sweep_threads)
+
+    def _tune_specs(self):
+        return [dict(self._spec)] if hasattr(self, "_spec") else [dict(s) for s in self.specs]
 
     def close(self):
         if getattr(self, "ctx", None) is not None:
@@ -595,6 +605,7 @@ class Batch:
     def __init__(self, runs, betas, thetas, resampler="systematic", seed=1, stream=None,
                  use_torch_memory=True, sweep_threads=None, graph=True):
         self.specs = [dict(r) for r in runs]
+        self._stream_obj = stream
         self.M = len(runs)
         self.betas = np.ascontiguousarray(betas, np.float64)
         self.thetas = np.ascontiguousarray(thetas, np.uint32)
@@ -616,9 +627,17 @@ class Batch:
             stream_ptr = stream.cuda_stream
         self.ctx = pa_batch_init(self.specs, self.betas, self.thetas, self.resampler, seed,
                                  stream_ptr, ws_ptr, ws_bytes)
+        if sweep_threads == "auto":  # the autotuner's choice for this shape (cached)
+            from . import tune
+            sweep_threads = tune.best_sweep_threads_batch(
+                self._tune_specs(), theta=int(np.median(self.thetas)) if len(self.thetas) else 0,
+                stream=getattr(self, "_stream_obj", None))
         if sweep_threads:
             pa_set_sweep_threads(self.ctx, sweep_threads)
         pa_set_graph(self.ctx, graph)
+
+    def _tune_specs(self):
+        return [dict(self._spec)] if hasattr(self, "_spec") else [dict(s) for s in self.specs]
 
     def close(self):
         if getattr(self, "ctx", None) is not None:

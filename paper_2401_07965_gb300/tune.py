@@ -10,6 +10,7 @@ memory and in a small JSON cache file.
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 
@@ -53,8 +54,33 @@ def _save():
 def best_sweep_threads(dim, L, R, couplings=("ferro",), theta=10, candidates=CANDIDATES,
                        rounds=2, use_cache=True, stream=None):
     """Threads per CTA of the fastest sweep for this shape (timed on the current device)."""
-    ea = couplings[0] != "ferro"
-    key = _key(dim, L, R, ea, theta)
+    return best_sweep_threads_batch([{"dim": dim, "L": L, "R": R, "couplings": couplings}],
+                                    theta=theta, candidates=candidates, rounds=rounds,
+                                    use_cache=use_cache, stream=stream)
+
+
+def _batch_key(specs, theta):
+    try:
+        import torch
+        dev = torch.cuda.get_device_name()
+    except Exception:
+        dev = "cuda"
+    if len(specs) == 1:
+        s = specs[0]
+        ea = s.get("couplings", ("ferro",))[0] != "ferro"
+        return _key(s["dim"], s["L"], s["R"], ea, theta)
+    shape = sorted((s["L"], s["R"], int(s.get("couplings", ("ferro",))[0] != "ferro"))
+                   for s in specs)
+    desc = hashlib.sha256(repr(shape).encode()).hexdigest()[:16]
+    return f"{dev}|batch|d{specs[0]['dim']}|M{len(specs)}|{desc}|theta{theta}"
+
+
+def best_sweep_threads_batch(specs, theta=10, candidates=CANDIDATES, rounds=2, use_cache=True,
+                             stream=None):
+    """Threads per CTA of the fastest sweep for a batch of runs (pa.Batch specs): every
+    candidate is timed on a throw-away batch of the same runs (results never depend on the
+    choice); the fastest is remembered per device and shape."""
+    key = _batch_key(specs, theta)
     if use_cache:
         _load()
         if key in _CACHE:
@@ -62,8 +88,8 @@ def best_sweep_threads(dim, L, R, couplings=("ferro",), theta=10, candidates=CAN
     n = rounds * len(candidates) + 1
     betas = np.linspace(0.0, 0.5, n + 1)
     thetas = np.full(n, theta, np.uint32)
-    run = pa.Population(dim, L, R, betas, thetas, "systematic", 12345, couplings=couplings,
-                        stream=stream)
+    run = pa.Batch([dict(s) for s in specs], betas, thetas, "systematic", 12345, stream=stream,
+                   graph=False)
     run.step(1)  # first launch of each kernel outside the timings
     best = {}
     pa.pa_enable_timing(run.ctx, True)
