@@ -74,6 +74,26 @@ PIPES = {"alu": (ALU_OPS_PER_SITEWORD, ALU_LANES_PER_SM),
          "issue": (ISSUE_PER_SITEWORD, ISSUE_LANES_PER_SM)}
 BINDING_PIPE = max(PIPES, key=lambda k: PIPES[k][0] / PIPES[k][1])
 ALU_OPS_PER_UPDATE = ALU_OPS_PER_SITEWORD / 32.0
+# d = 3 (six bonds, classes dE = 4, 8, 12): per site 22 logic operations (six
+# neighbour XORs, the bit-sliced count of unsatisfied bonds, the class masks, the
+# flip) and per plane one multiply and two multiply-adds for the threshold word
+PIPES3 = {"alu": (22 + E_BLOCKS * (17 + 4 * 2), ALU_LANES_PER_SM),
+          "fma": (2 * MULWIDE_PER_SITEWORD + E_BLOCKS * 4 * 3, FMA_LANES_PER_SM),
+          "issue": (22 + E_BLOCKS * (17 + 4 * 2) + MULWIDE_PER_SITEWORD + E_BLOCKS * 4 * 3,
+                    ISSUE_LANES_PER_SM)}
+
+
+def roofline_record(pipes, rate, nsm, f_hz):
+    """Binding pipe of the per-site-word demand `pipes` and the fraction reached at `rate`
+    spin updates/ns."""
+    bind = max(pipes, key=lambda k: pipes[k][0] / pipes[k][1])
+    per_sw, lanes = pipes[bind]
+    peak = nsm * lanes * f_hz / 1e12
+    achieved = per_sw / 32.0 * rate * 1e9 / 1e12
+    return {"bound": "alu", "binding_pipe": bind, "achieved": achieved, "peak": peak,
+            "unit": "T lane-ops/s", "frac": achieved / peak,
+            "roofline_updates_per_ns": peak * 1e3 * 32.0 / per_sw,
+            "per_site_word": {k: v[0] for k, v in pipes.items()}}
 
 
 def _env_rank():
@@ -367,6 +387,9 @@ def run_ours(args):
     e2e = None if args.no_e2e else run_e2e(args, pa, stream, seed, dev, threads)
     # time to a free energy within 1e-4 per spin of Kaufman's value (L=64)
     acc = None if (args.no_accuracy or world > 1) else accuracy_l64(pa, dev)
+    # the batched 3D spin-glass workload (192 runs), 20 steps spread over its schedule
+    ea3d = None if (args.no_ea3d or world > 1) else ea3d_batch(pa, stream, 64, 20, 5,
+                                                               timed_sweeps=True)
 
     if rank != 0:
         if world > 1:
@@ -396,6 +419,9 @@ def run_ours(args):
             "sweep_launches_timed": sweep_n,
             "roofline_updates_per_ns": peak * 1e3 * 32.0 / per_sw,
             "sweep_share_of_step_time": sweep_ms / total_ms if world == 1 else None}
+    if ea3d and "sweep_updates_per_ns" in ea3d:
+        ea3d["roofline"] = roofline_record(PIPES3, ea3d["sweep_updates_per_ns"], nsm, f_hz)
+        ea3d["roofline"]["kernel"] = "k_sweep3d<L,true> (L = 4, 6, 8; grouped replicas)"
     cpu = cpu_mt = None
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_baseline(64, 5, parallel=False)
@@ -414,7 +440,7 @@ def run_ours(args):
                        "sweep_threads": threads,
                        "parallelism": f"{world} independent runs" if world > 1 else "1 run"},
             "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_mt": cpu_mt, "e2e": e2e,
-            "time_to_1e4": acc, "clocks": clocks, "gpu_launches": launches}
+            "time_to_1e4": acc, "ea3d": ea3d, "clocks": clocks, "gpu_launches": launches}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -475,30 +501,66 @@ def _line(workload, value, ms, steps, warmup, extra):
     print(json.dumps(line), flush=True)
 
 
-def run_ea3d(args):
-    """3D Edwards-Anderson +-J, L in {4, 6, 8} periodic, 64 disorder realizations per L
-    (couplings iid +-1 from disorder seed 3), R=50000 each, beta 0 -> 3 in 300 steps,
-    theta=10, systematic: 192 runs advanced by the same kernels, steps replayed as graphs."""
+def ea3d_batch(pa, stream, realizations=64, steps=20, warmup=5, timed_sweeps=False):
+    """The 3D spin-glass batch (L = 4, 6, 8 periodic, `realizations` disorder realizations
+    per L from disorder seed 3, R = 50000 each, beta 0 -> 3 in 300 steps, theta = 10,
+    systematic): `steps` temperature steps spread evenly over the schedule are timed
+    (CUDA events around each graph-replayed step; the runs advance through all 300).
+    Returns spin updates/ns of the timed steps (and of the sweep kernels alone)."""
     import torch
-    from paper_2401_07965_gb300 import pa
     n = 300
     betas = np.linspace(0.0, 3.0, n + 1)
     thetas = np.full(n, 10, np.uint32)
     runs = [{"dim": 3, "L": L, "R": 50000, "couplings": ("ea", 3, 64 * k + r), "ensemble": k}
-            for k, L in enumerate((4, 6, 8)) for r in range(64)]
-    stream = torch.cuda.current_stream()
+            for k, L in enumerate((4, 6, 8)) for r in range(realizations)]
     b = pa.Batch(runs, betas, thetas, "systematic", 1000, stream=stream, sweep_threads="auto")
-    K = min(args.steps, n - args.warmup)
-    b.step(args.warmup)
-    ms = _timed_batch(pa, b, K, stream)
-    i0, i1 = args.warmup, args.warmup + K
-    upd = float(sum(10 * (L ** 3) * 50000 for L in (4, 6, 8) for _ in range(64)) * K)
-    obs = [b.observables(m) for m in (0, 64, 128)]
+    b.step(warmup)
+    first = warmup + 1
+    timed = sorted({first + int((k + 0.5) * (n - warmup) / steps) for k in range(steps)})
+    timed = [t for t in timed if t <= n]
+    upd_step = float(sum(10 * (L ** 3) * 50000 for L in (4, 6, 8)) * realizations)
+    ms, sweep_ms, done = 0.0, 0.0, warmup
+    for t in timed:
+        if t - 1 > done:
+            b.step(t - 1 - done)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if timed_sweeps:
+            pa.pa_enable_timing(b.ctx, True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        if timed_sweeps:
+            sm, _, _ = pa.pa_sweep_timing(b.ctx)
+            sweep_ms += sm
+            pa.pa_enable_timing(b.ctx, False)
+        done = t
+    R_check = [b.observables(m)["R_i"] for m in (0, realizations, 2 * realizations)]
     b.close()
-    _line("3D EA +-J, L=4/6/8 x 64 realizations, R=50000 each, beta 0->3 in 300 steps, "
-          f"theta=10, systematic; timed steps {i0 + 1}..{i1}", upd / (ms * 1e6), ms, K,
-          args.warmup, {"runs": len(runs), "graph": True,
-                        "R_i_check": [o["R_i"] for o in obs]})
+    out = {"updates_per_ns": upd_step * len(timed) / (ms * 1e6), "ms_per_step": ms / len(timed),
+           "timed_steps": timed, "runs": len(runs), "R_i_check": R_check}
+    if timed_sweeps:
+        out["sweep_updates_per_ns"] = upd_step * len(timed) / (sweep_ms * 1e6)
+        out["sweep_share_of_step_time"] = sweep_ms / ms
+    return out
+
+
+def run_ea3d(args):
+    """3D Edwards-Anderson +-J, L in {4, 6, 8} periodic, 64 disorder realizations per L
+    (couplings iid +-1 from disorder seed 3), R=50000 each, beta 0 -> 3 in 300 steps,
+    theta=10, systematic: 192 runs advanced by the same kernels, steps replayed as graphs;
+    K steps spread over the schedule are timed."""
+    import torch
+    from paper_2401_07965_gb300 import pa
+    stream = torch.cuda.current_stream()
+    K = args.steps if args.steps != 1000 else 30
+    res = ea3d_batch(pa, stream, args.realizations, K, args.warmup, timed_sweeps=True)
+    _line(f"3D EA +-J, L=4/6/8 x {args.realizations} realizations, R=50000 each, beta 0->3 "
+          "in 300 steps, theta=10, systematic", res["updates_per_ns"],
+          res["ms_per_step"] * len(res["timed_steps"]), len(res["timed_steps"]), args.warmup,
+          {"ea3d": res, "graph": True})
     return 0
 
 
@@ -722,29 +784,55 @@ def _schedule_arm(pa, CT, sysdef, seeds, stream, plain=None, learned=None, bits=
     return out
 
 
-def _summ(rows, ref_mbf, ref_e, N):
+def _boot_rms(err, rng, nboot=2000):
+    """Bootstrap (over seeds) standard error of the root-mean-square of err."""
+    idx = rng.integers(0, len(err), size=(nboot, len(err)))
+    return float(np.sqrt((err[idx] ** 2).mean(axis=1)).std(ddof=1))
+
+
+def _summ(rows, ref_mbf, ref_e, N, rng):
     err = np.array([(r["mbf"] - ref_mbf) / N for r in rows])
+    ms = np.array([r["ms"] for r in rows])
     out = {"rms_f_err_per_spin": float(np.sqrt(np.mean(err ** 2))),
+           "rms_se": _boot_rms(err, rng),
            "mean_f_err_per_spin": float(err.mean()),
+           "mean_se": float(err.std(ddof=1) / np.sqrt(len(err))),
            "rho_t_over_R": float(np.mean([r["rho"] for r in rows])),
-           "ms": float(np.mean([r["ms"] for r in rows])),
+           "ms": float(ms.mean()), "ms_se": float(ms.std(ddof=1) / np.sqrt(len(ms))),
            "steps": float(np.mean([r["steps"] for r in rows])),
            "sweeps": float(np.mean([r["sweeps"] for r in rows])), "seeds": len(rows)}
     if ref_e is not None:
         out["rms_e_err"] = float(np.sqrt(np.mean([(r["e"] - ref_e) ** 2 for r in rows])))
+    out["_err"] = err
     return out
 
 
+def _compare(arm, plain, rng, nboot=2000):
+    """Learned arm against the plain arm (independent seeds): the difference of the rms
+    errors with its bootstrap standard error, and whether the learned arm is better (or
+    not worse) by more than two standard errors."""
+    a, b = arm["_err"], plain["_err"]
+    ia = rng.integers(0, len(a), size=(nboot, len(a)))
+    ib = rng.integers(0, len(b), size=(nboot, len(b)))
+    d = np.sqrt((a[ia] ** 2).mean(axis=1)) - np.sqrt((b[ib] ** 2).mean(axis=1))
+    diff = arm["rms_f_err_per_spin"] - plain["rms_f_err_per_spin"]
+    se = float(d.std(ddof=1))
+    return {"rms_diff": diff, "rms_diff_se": se,
+            "better_by_2se": bool(diff < -2 * se), "worse_by_2se": bool(diff > 2 * se),
+            "time_ratio": arm["ms"] / plain["ms"]}
+
+
 def run_controller(args):
-    """The learned schedule controller against the plain schedule.
+    """The learned schedule controller against the plain schedule, with bootstrap errors.
 
     3D +-J spin glass L=10 (disorder seed 5, realization 0), R=100000, beta 0 -> 3: plain 300
     steps of 10 sweeps against the learned schedule on a 600-point grid with the same 3000
-    sweeps, and with 2250 and 1500; errors against one R=10^6 run (600 steps, 30 sweeps).
-    2D Ising L=64, R=10000, beta 0 -> 1: plain 200 steps of 10 sweeps against the learned
-    schedule on an 800-point grid with 2000, 1500 and 1000 sweeps; errors against Kaufman's
-    exact free energy.  Value: device time of the cheapest learned schedule whose
-    root-mean-square free-energy error is at most the plain schedule's (spin glass)."""
+    sweeps, and with 2250 and 1500; errors against the mean of four R=10^6 runs (600 steps,
+    30 sweeps; no exact value exists).  2D Ising L=64, R=10000, beta 0 -> 1: plain 200 steps
+    of 10 sweeps against the learned schedule on an 800-point grid with 2000, 1500 and 1000
+    sweeps; errors against Kaufman's exact free energy.  --seeds independent seeds per arm.
+    Value: device time of the cheapest learned schedule whose rms free-energy error (3D EA
+    L=10) is not worse than the plain schedule's by two bootstrap standard errors."""
     import torch
     from paper_2401_07965_gb300 import controller as CT
     from paper_2401_07965_gb300 import pa
@@ -754,43 +842,57 @@ def run_controller(args):
         return 1
     bits = CT.load()
     stream = torch.cuda.Stream()
+    rng = np.random.default_rng(2024)
     S = args.seeds
     seeds = range(1, S + 1)
     res = {}
     # spin glass, config of the learned-schedule benchmark
     ea = (3, 10, ("ea", 5, 0), 100000, 3.0)
-    ref = _schedule_arm(pa, CT, (3, 10, ("ea", 5, 0), 1000000, 3.0), [4242], stream,
-                        plain=(600, 30))[0]
+    refs = _schedule_arm(pa, CT, (3, 10, ("ea", 5, 0), 1000000, 3.0), [4242, 4243, 4244, 4245],
+                         stream, plain=(600, 30))
+    ref_mbf = float(np.mean([r["mbf"] for r in refs]))
+    ref_e = float(np.mean([r["e"] for r in refs]))
     N = 1000
-    res["ea10"] = {"reference": {"R": 1000000, "steps": 600, "theta": 30, "mbf": ref["mbf"],
-                                 "e": ref["e"], "ms": ref["ms"]}}
+    res["ea10"] = {"reference": {"R": 1000000, "runs": len(refs), "steps": 600, "theta": 30,
+                                 "mbf": ref_mbf, "mbf_se": float(np.std([r["mbf"] for r in refs],
+                                                                        ddof=1) / 2.0),
+                                 "e": ref_e, "ms": float(np.mean([r["ms"] for r in refs]))}}
     res["ea10"]["plain"] = _summ(_schedule_arm(pa, CT, ea, seeds, stream, plain=(300, 10)),
-                                 ref["mbf"], ref["e"], N)
+                                 ref_mbf, ref_e, N, rng)
     for budget in (3000, 2250, 1500):
         res["ea10"][f"learned_{budget}"] = _summ(
             _schedule_arm(pa, CT, ea, seeds, stream, learned=(600, 2, 10, budget), bits=bits),
-            ref["mbf"], ref["e"], N)
+            ref_mbf, ref_e, N, rng)
     # 2D Ising, exact reference
     L = 64
     exact = _kaufman(L, 1.0)
     ising = (2, L, ("ferro",), 10000, 1.0)
     res["ising64"] = {"plain": _summ(_schedule_arm(pa, CT, ising, seeds, stream,
-                                                   plain=(200, 10)), exact, None, L * L)}
+                                                   plain=(200, 10)), exact, None, L * L, rng)}
     for budget in (2000, 1500, 1000):
         res["ising64"][f"learned_{budget}"] = _summ(
             _schedule_arm(pa, CT, ising, seeds, stream, learned=(800, 4, 10, budget), bits=bits),
-            exact, None, L * L)
+            exact, None, L * L, rng)
+    for sysname in ("ea10", "ising64"):
+        plain = res[sysname]["plain"]
+        for key in list(res[sysname]):
+            if key.startswith("learned_"):
+                res[sysname][key]["vs_plain"] = _compare(res[sysname][key], plain, rng)
+    for sysname in ("ea10", "ising64"):
+        for key, arm in res[sysname].items():
+            arm.pop("_err", None)
     p_ea = res["ea10"]["plain"]
     ok = [res["ea10"][f"learned_{b}"] for b in (3000, 2250, 1500)
-          if res["ea10"][f"learned_{b}"]["rms_f_err_per_spin"] <= p_ea["rms_f_err_per_spin"]]
+          if not res["ea10"][f"learned_{b}"]["vs_plain"]["worse_by_2se"]]
     best = min(ok, key=lambda r: r["ms"]) if ok else None
     _line("learned vs plain schedule: 3D EA +-J L=10, R=100000, beta 0->3, plain 300 steps x "
           "10 sweeps vs learned on a 600-point grid at 3000/2250/1500 sweeps; 2D Ising L=64, "
-          f"R=10000, beta 0->1 vs Kaufman; {S} seeds each",
+          f"R=10000, beta 0->1 vs Kaufman; {S} seeds each, bootstrap standard errors",
           best["ms"] if best else None, best["ms"] if best else 0.0, 0, 0,
           {"unit": "ms", "higher_is_better": False,
            "what": "device ms per run of the cheapest learned schedule whose rms free-energy "
-                   "error (3D EA L=10) is at most the plain 3000-sweep schedule's",
+                   "error (3D EA L=10) is not worse than the plain 3000-sweep schedule's by two "
+                   "bootstrap standard errors",
            "plain_ms": p_ea["ms"], "results": res})
     return 0
 
@@ -948,8 +1050,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the time-to-1e-4 sub-record of the headline line")
+    ap.add_argument("--no-ea3d", action="store_true",
+                    help="skip the batched 3D spin-glass sub-record of the headline line")
     ap.add_argument("--threads", type=int, default=0, help="small case: sweep threads per CTA")
     ap.add_argument("--replicas", type=int, default=20000, help="small case: population size")
+    ap.add_argument("--realizations", type=int, default=64,
+                    help="ea3d workload: disorder realizations per lattice size")
     ap.add_argument("--seeds", type=int, default=24, help="controller workload: seeds per arm")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: one run of R=20000 replicas of the same lattice (profiling)")

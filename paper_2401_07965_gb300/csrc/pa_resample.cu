@@ -67,7 +67,9 @@ __device__ __forceinline__ bool le128(U128 a, U128 b) { return !lt128(b, a); }
 // with xR = aT + b, that is a + [b 2^32 > u T], at most R.
 __device__ uint64_t sys_below(uint64_t x, uint64_t R, uint64_t T, uint32_t u) {
     const U128 P = mul128(x, R);
-    uint64_t a = (uint64_t)(__ddiv_rn(__dmul_rn((double)x, (double)R), (double)T));
+    // a = floor(xR / T) <= R < 2^24: an FP32 estimate is within a few units (FP64 is
+    // slow on this part), and the 128-bit corrections below make it exact
+    uint64_t a = (uint64_t)__fdiv_rn(__fmul_rn((float)x, (float)R), (float)T);
     for (int it = 0; it < 8 && lt128(P, mul128(a, T)); ++it) --a;
     for (int it = 0; it < 8 && le128(mul128(a + 1, T), P); ++it) ++a;
     const uint64_t b = P.lo - a * T;  // < T, exact in the low 64 bits
@@ -707,9 +709,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scatter(KParams p) {
 // --------------------------------------------------------------------------
 // family statistics of the new population (families stay sorted by slot)
 // --------------------------------------------------------------------------
+template <bool PARTIAL>
 __device__ void finish_run(const KParams& p, const RunDesc& r, DevState* st, int mode, double* a,
                            double* b, double* ws);
 
+// PARTIAL: partial resampling (weighted sums); a separate instance keeps the
+// registers of the plain step's kernel low
+template <bool PARTIAL>
 __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
     const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
     const uint32_t b = blockIdx.x - r.blk0;
@@ -721,25 +727,61 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
     const int i = (mode == 0) ? st->step + 1 : st->step;
     const uint32_t Ri = st->R_cur;
     const uint32_t* fam = r.fam[i & 1];
-    if (threadIdx.x == 0) sc2 = 0ull;
-    __syncthreads();
     const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    // Families stay sorted by slot, so a family is a run of equal values.  The
+    // block's slots go to shared memory; each run start finds its end from the
+    // 32-slot masks of run starts, and only the block's last run, which may go on
+    // past the block, searches the array beyond it.  c ln c of small families
+    // comes from a table.
+    constexpr int FTAB = 64;
+    __shared__ uint32_t sf[SCAN_CHUNK];
+    __shared__ uint32_t smask[SCAN_CHUNK / 32];
+    __shared__ double clt[FTAB + 1];
+    const uint32_t B0 = b * SCAN_CHUNK;
+    const uint32_t nin = B0 < Ri ? min((uint32_t)SCAN_CHUNK, Ri - B0) : 0u;
+    if (threadIdx.x == 0) sc2 = 0ull;
+    for (int c = threadIdx.x; c <= FTAB; c += blockDim.x)
+        clt[c] = c > 1 ? __dmul_rn((double)c, log((double)c)) : 0.0;
+    for (int l = threadIdx.x; l < SCAN_CHUNK; l += blockDim.x)
+        sf[l] = (uint32_t)l < nin ? fam[B0 + l] : 0xFFFFFFFFu;
+    __syncthreads();
+    const uint32_t before = (B0 > 0 && nin) ? fam[B0 - 1] : 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rnd = 0; rnd < SCAN_CHUNK / SCAN_THREADS; ++rnd) {
+        const int l = rnd * SCAN_THREADS + warp * 32 + lane;
+        const bool st_l = (uint32_t)l < nin && (l == 0 ? (B0 == 0 || before != sf[0])
+                                                       : sf[l - 1] != sf[l]);
+        const uint32_t m = __ballot_sync(0xffffffffu, st_l);
+        if (lane == 0) smask[rnd * (SCAN_THREADS / 32) + warp] = m;
+    }
+    __syncthreads();
     double cl = 0.0;
     unsigned long long c2 = 0;
-    for (int e = 0; e < SCAN_ITEMS; ++e) {
-        const uint32_t dslot = (uint32_t)(j0 + e);
-        if (dslot >= Ri) break;
-        const uint32_t f = fam[dslot];
-        if (dslot > 0 && fam[dslot - 1] == f) continue;
-        uint32_t lo = dslot + 1, hi = Ri;  // first index past the run of f
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (fam[mid] == f) lo = mid + 1;
-            else hi = mid;
+    for (int rnd = 0; rnd < SCAN_CHUNK / SCAN_THREADS; ++rnd) {
+        const int l = rnd * SCAN_THREADS + warp * 32 + lane;
+        int q = l >> 5;
+        const int bit = l & 31;
+        if (!((smask[q] >> bit) & 1u)) continue;  // not a run start (or past R_i)
+        uint32_t m = bit == 31 ? 0u : (smask[q] & (0xFFFFFFFFu << (bit + 1)));
+        while (m == 0u && q + 1 < SCAN_CHUNK / 32) m = smask[++q];
+        uint64_t c;
+        if (m) {
+            c = (uint64_t)(q * 32 + __ffs(m) - 1 - l);
+        } else {  // the block's last run: it may continue past the block
+            uint32_t lo = B0 + nin, hi = Ri;
+            const uint32_t f = sf[l];
+            if (lo < hi && fam[lo] == f) {
+                ++lo;
+                while (lo < hi) {  // first index past the run of f
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (fam[mid] == f) lo = mid + 1;
+                    else hi = mid;
+                }
+            }
+            c = (uint64_t)(lo - (B0 + l));
         }
-        const uint64_t c = lo - dslot;
         c2 += c * c;
-        if (c > 1) cl = __dadd_rn(cl, __dmul_rn((double)c, log((double)c)));
+        if (c > 1) cl = __dadd_rn(cl, c <= FTAB ? clt[c] : __dmul_rn((double)c, log((double)c)));
     }
     for (int o = 16; o > 0; o >>= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
     if ((threadIdx.x & 31) == 0 && c2) atomicAdd(&sc2, c2);
@@ -753,7 +795,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
         r.partCL[b] = sd[0];
         if (sc2) atomicAdd(&r.trace[i].sumC2, sc2);
     }
-    if (p.alpha >= 0.0) {
+    if (PARTIAL) {
         // partial resampling: the new population's weights (1 after a
         // resampling, else the kept weight rescaled by 2^-wexp), then the
         // block's tree sums of w, w E, w E^2, w |M|, w M^2
@@ -793,11 +835,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
     if (!last) return;
     if (threadIdx.x == 0) r.tick[1] = 0u;
     __threadfence();
-    finish_run(p, r, st, mode, fa, fb, sd);
+    finish_run<PARTIAL>(p, r, st, mode, fa, fb, sd);
 }
 
 // fixed-order sums of the run's per-block partials, close the step (one CTA of
 // SCAN_THREADS threads; a, b, ws: shared arrays of SCAN_THREADS doubles)
+template <bool PARTIAL>
 __device__ void finish_run(const KParams& p, const RunDesc& r, DevState* st, int mode, double* a,
                            double* b, double* ws) {
     const int i = (mode == 0) ? st->step + 1 : st->step;
@@ -816,7 +859,7 @@ __device__ void finish_run(const KParams& p, const RunDesc& r, DevState* st, int
         }
         __syncthreads();
     }
-    if (p.alpha >= 0.0) {
+    if (PARTIAL) {
         // partial resampling: tree over the blocks' weighted sums
         // (PARTIAL_MAX_BLOCKS leaves in all, zero past the run's blocks)
         const int nb = r.nblk;
@@ -1178,7 +1221,8 @@ cudaError_t launch_partial_init(const KParams& p, cudaStream_t s) {
 }
 
 cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int64_t* launches) {
-    k_family<<<p.nblk_total, SCAN_THREADS, 0, s>>>(p, mode);
+    if (p.alpha >= 0.0) k_family<true><<<p.nblk_total, SCAN_THREADS, 0, s>>>(p, mode);
+    else k_family<false><<<p.nblk_total, SCAN_THREADS, 0, s>>>(p, mode);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
