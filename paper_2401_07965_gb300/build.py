@@ -18,7 +18,7 @@ LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libpa.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["pa_sweep.cu", "pa_sweep2d.cu", "pa_resample.cu", "pa_api.cu", "pa_static.cu", "pa_weighted.cu", "pa_control.cu",
+SOURCES = ["pa_sweep.cu", "pa_sweep2d.cu", "pa_sweep3d.cu", "pa_resample.cu", "pa_api.cu", "pa_static.cu", "pa_weighted.cu", "pa_control.cu",
            "pa_overlap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",

@@ -29,6 +29,7 @@ struct RunHost {
     int L, N, W, Wp, nlev, P;
     uint32_t R, Rcap;
     int nblk, ngrp;
+    int g3, nct3;            // 3D kernel: replica groups per CTA, CTAs (0: not eligible)
     int ensemble;
     std::vector<uint8_t> jb;
     int parity;
@@ -42,7 +43,7 @@ enum Region {
 
 enum Shared {
     S_RUNS, S_B2R, S_G2R, S_BETA, S_DBETA, S_Q, S_THR, S_THETA, S_IDS, S_WOUT,
-    S_CTL, S_GBETA, S_GTHR, S_GDB, S_GQ, S_PAIRS, S_POV, S_OVACC, S_OVTICK, S_COUNT
+    S_CTL, S_GBETA, S_GTHR, S_GDB, S_GQ, S_PAIRS, S_POV, S_OVACC, S_OVTICK, S_C3, S_COUNT
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -146,6 +147,8 @@ pa_status make_runs(const pa_run_spec* specs, int M, int method, std::vector<Run
         if (h.Rcap > MAX_POPULATION) return PA_ERR_LIMIT;
         h.nblk = (int)((h.Rcap + SCAN_CHUNK - 1) / SCAN_CHUNK);
         h.ngrp = (int)((h.Rcap + 31) / 32);
+        h.g3 = (*d == 3) ? sweep3d_groups(h.L) : 0;
+        h.nct3 = h.g3 ? (h.ngrp + h.g3 - 1) / h.g3 : 0;
         h.ensemble = s.ensemble;
         h.parity = 0;
         out->push_back(std::move(h));
@@ -181,6 +184,9 @@ Layout make_layout(const std::vector<RunHost>& runs, int n_steps) {
     sz[S_POV] = (size_t)(maxN + 1) * 8;
     sz[S_OVACC] = M * (size_t)(maxN + 1) * 4;  // overlap accumulators, zero between calls
     sz[S_OVTICK] = M * 4;
+    size_t nct3 = 0;
+    for (const RunHost& h : runs) nct3 += (size_t)h.nct3;
+    sz[S_C3] = nct3 * 4;
     size_t o = 0;
     for (int r = 0; r < S_COUNT; ++r) {
         L.shared_off[r] = o;
@@ -623,6 +629,34 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     p.nblk_total = blk0;
     p.ngrp_total = grp0;
 
+    // 3D runs of sides 4..16: the grouped 3D kernel, one launch per distinct side
+    // (at most four), each over the CTAs of the runs of that side in run order
+    std::vector<uint32_t> c3;
+    {
+        std::vector<int> Ls;
+        bool ok = d == 3;
+        for (const RunHost& h : ctx->runs) {
+            if (!h.g3) ok = false;
+            if (std::find(Ls.begin(), Ls.end(), h.L) == Ls.end()) Ls.push_back(h.L);
+        }
+        if (ok && Ls.size() <= 4) {
+            uint32_t* base3 = (uint32_t*)(base + lay.shared_off[S_C3]);
+            p.n3 = (int)Ls.size();
+            for (int k = 0; k < p.n3; ++k) {
+                p.L3[k] = Ls[k];
+                p.c3map[k] = base3 + c3.size();
+                uint32_t n = 0;
+                for (int m = 0; m < M; ++m) {
+                    if (ctx->runs[m].L != Ls[k]) continue;
+                    ctx->desc[m].cta0 = n;
+                    for (int c = 0; c < ctx->runs[m].nct3; ++c) c3.push_back((uint32_t)m);
+                    n += (uint32_t)ctx->runs[m].nct3;
+                }
+                p.n3cta[k] = n;
+            }
+        }
+    }
+
     // per-step tables: dbeta, q = exp(-4 dbeta), Metropolis thresholds at beta_i
     std::vector<double> dbeta(n), q(n);
     std::vector<uint32_t> thr((size_t)4 * n);
@@ -640,6 +674,7 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     up(p.runs, ctx->desc.data(), sizeof(RunDesc) * M);
     up(p.blk2run, b2r.data(), b2r.size() * 4);
     up(p.grp2run, g2r.data(), g2r.size() * 4);
+    if (!c3.empty()) up(p.c3map[0], c3.data(), c3.size() * 4);
     up(p.beta, ctx->beta.data(), sizeof(double) * (n + 1));
     up(p.dbeta, dbeta.data(), sizeof(double) * n);
     up(p.q, q.data(), sizeof(double) * n);

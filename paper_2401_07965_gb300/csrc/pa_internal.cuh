@@ -158,6 +158,7 @@ struct RunDesc {
     uint32_t blk0;           // its first block in the flattened scan grids
     uint32_t grp0;           // its first CTA in the flattened sweep grid (= slot_base / 32)
     uint32_t run;            // run index
+    uint32_t cta0;           // 3D kernel: its first CTA in the launch for its side
     uint32_t* spins[2];
     int32_t* E[2];
     uint32_t* fam[2];
@@ -211,6 +212,11 @@ struct KParams {
     double alpha;            // partial resampling threshold (< 0: resample every step)
     int qcap_limit;          // sweep: cap on the undecided-site queue (< 0: its full size)
     int L_all;               // the side L shared by every run of the batch (0 if they differ)
+    // 3D kernel plan: one launch per distinct side (n3 = 0: the general kernel)
+    int n3;
+    int L3[4];
+    const uint32_t* c3map[4];  // CTA -> run of each launch
+    uint32_t n3cta[4];
 };
 
 // partial resampling: blocks of a run whose tree sums one CTA can finish
@@ -234,6 +240,9 @@ cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int
 cudaError_t prepare_sweep(const KParams& p, int threads);
 cudaError_t launch_sweep2d(const KParams& p, int threads, cudaStream_t s, bool attr_only,
                            bool* done);
+int sweep3d_groups(int L);
+cudaError_t launch_sweep3d(const KParams& p, int L, const uint32_t* cta2run, uint32_t ncta,
+                           cudaStream_t s, bool attr_only);
 cudaError_t launch_control(const KParams& p, cudaStream_t s);
 int sweep_threads(int N);
 bool sweep_threads_supported(int t);

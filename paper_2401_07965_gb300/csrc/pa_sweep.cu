@@ -514,6 +514,9 @@ cudaError_t prepare_sweep(const KParams& p, int threads) {
     bool done = false;
     cudaError_t e = launch_sweep2d(p, threads, nullptr, true, &done);
     if (e != cudaSuccess) return e;
+    for (int k = 0; k < p.n3 && e == cudaSuccess; ++k)
+        e = launch_sweep3d(p, p.L3[k], p.c3map[k], p.n3cta[k], nullptr, true);
+    if (e != cudaSuccess) return e;
     if (p.d == 2) return p.ea ? prepare_t<2, true>(threads) : prepare_t<2, false>(threads);
     return p.ea ? prepare_t<3, true>(threads) : prepare_t<3, false>(threads);
 }
@@ -534,6 +537,12 @@ cudaError_t launch_measure(const KParams& p, int threads, cudaStream_t s) {
 }
 
 cudaError_t launch_sweep(const KParams& p, int threads, cudaStream_t s) {
+    if (p.n3 > 0) {  // 3D runs of sides 4..16: one launch per side
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < p.n3 && e == cudaSuccess; ++k)
+            e = launch_sweep3d(p, p.L3[k], p.c3map[k], p.n3cta[k], s, false);
+        return e;
+    }
     bool done = false;
     const cudaError_t e = launch_sweep2d(p, threads, s, false, &done);
     if (e != cudaSuccess || done) return e;

@@ -1,0 +1,556 @@
+// pa_sweep3d.cu -- the temperature step's replica copy, theta checkerboard
+// Metropolis sweeps and measurement (Sec. 2 steps 2-4) for three-dimensional
+// runs of side 4 <= L <= 16: the work of k_group's sweep mode with a layout for
+// small lattices.  Random numbers, decisions and results are the same.
+//
+// Grouping.  A 3D lattice of a few hundred sites gives one group of 32 replicas
+// too little work per half-sweep (and per barrier), so a CTA of 128 threads
+// holds G replica groups of one run (G = 8, 4, 2, 1 for L = 4, 6, 8, >= 10):
+// G halo-padded multi-spin lattices in shared memory (cell (x, y, z),
+// -1 <= x, y, z <= L, word ((z+1)(L+2) + y+1)(L+2) + x+1), each group keeping
+// its own Philox counter (its global replica group).  Every neighbour of an
+// interior site is at a fixed offset +-1, +-(L+2), +-(L+2)^2; a flip of a
+// boundary site also writes its copies in the halo faces.
+//
+// Walk.  A per-colour table lists the G x N/2 sites of the colour (lattice
+// word, group, Philox site index, boundary faces); thread t takes entries
+// t, t + 128, ...  Undecided sites after eight planes go to per-warp queues
+// and are finished by the same warp (branch-free first pass, as in 2D).
+//
+// Energy classes of d = 3 (n unsatisfied bonds of 6): dE = 4 (n = 2), 8 (n = 1),
+// 12 (n = 0), disjoint masks, so a plane's threshold bit word is the sum
+// c4 b4 + c8 b8 + c12 b12 (multiply-adds on the multiply pipe).
+#include "pa_sweep_common.cuh"
+
+namespace pa {
+namespace {
+
+constexpr int NT3 = 128;
+
+template <int L>
+struct Shape3 {
+    static constexpr int P = L + 2, P2 = P * P, N = L * L * L, H = N / 2;
+    static constexpr int G = (4 * NT3) / H >= 8 ? 8 : ((4 * NT3) / H >= 1 ? (4 * NT3) / H : 1);
+    static constexpr int ITERS = (G * H + NT3 - 1) / NT3;
+    static constexpr int W = (N + 31) / 32, WP = (W + 3) & ~3;
+    static constexpr int CELLS = P * P * P;
+    static constexpr int LAT_WORDS = (G * CELLS + 3) & ~3;
+    static constexpr int QW = (32 * ITERS) / 4 + 32;          // per warp, then 32 scratch slots
+    static constexpr int TAB = G * H;                         // table entries per colour
+    __host__ __device__ static constexpr int cell(int x, int y, int z) {
+        return ((z + 1) * P + y + 1) * P + x + 1;
+    }
+};
+
+// Philox table of one plane block (site-independent round-3 values) and the
+// threshold bits (0/1) of its planes for dE = 4, 8, 12
+struct Tab3 {
+    uint32_t c0k, c1, c2k, pad;
+    uint32_t B0[4], B1[4], B2[4];
+};
+
+__device__ __forceinline__ void build_tab3(Tab3* tab, int g, const KParams& p, uint32_t grp,
+                                           uint32_t step, uint32_t t, int colour,
+                                           const uint32_t* thr) {
+    uint32_t h0a, l0a, h1a, l1a, h0b, l0b, h1c, l1c;
+    mulhilo(PHILOX_M0, grp, h0a, l0a);
+    mulhilo(PHILOX_M1, step, h1a, l1a);
+    const uint32_t c1v = DOM_SWEEP | (t << 4) | ((uint32_t)colour << 3) | (uint32_t)g;
+    const uint32_t A0 = h1a ^ c1v ^ p.rk0[0];
+    mulhilo(PHILOX_M0, A0, h0b, l0b);
+    const uint32_t B2 = h0b ^ l0a ^ p.rk1[1];
+    mulhilo(PHILOX_M1, B2, h1c, l1c);
+    Tab3 e;
+    e.c0k = h1c ^ p.rk0[2];
+    e.c1 = l1c;
+    e.c2k = l0b ^ p.rk1[2];
+    e.pad = 0u;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int sh = 31 - (4 * g + m);
+        e.B0[m] = (thr[1] >> sh) & 1u;
+        e.B1[m] = (thr[2] >> sh) & 1u;
+        e.B2[m] = (thr[3] >> sh) & 1u;
+    }
+    tab[g] = e;
+}
+
+__device__ __forceinline__ void draw2_3(const Tab3& e, const Tab3& f, uint32_t B1, uint32_t h0c,
+                                        uint32_t l0c, const KParams& p, uint32_t (&W)[4],
+                                        uint32_t (&V)[4]) {
+    uint32_t x0 = e.c0k ^ B1, x1 = e.c1, x2 = h0c ^ e.c2k, x3 = l0c;
+    uint32_t y0 = f.c0k ^ B1, y1 = f.c1, y2 = h0c ^ f.c2k, y3 = l0c;
+#pragma unroll
+    for (int rr = 3; rr < 10; ++rr) {
+        uint32_t hi0, lo0, hi1, lo1, gi0, go0, gi1, go1;
+        mulhilo(PHILOX_M0, x0, hi0, lo0);
+        mulhilo(PHILOX_M1, x2, hi1, lo1);
+        mulhilo(PHILOX_M0, y0, gi0, go0);
+        mulhilo(PHILOX_M1, y2, gi1, go1);
+        x0 = hi1 ^ x1 ^ p.rk0[rr];
+        x1 = lo1;
+        x2 = hi0 ^ x3 ^ p.rk1[rr];
+        x3 = lo0;
+        y0 = gi1 ^ y1 ^ p.rk0[rr];
+        y1 = go1;
+        y2 = gi0 ^ y3 ^ p.rk1[rr];
+        y3 = go0;
+    }
+    W[0] = x0; W[1] = x1; W[2] = x2; W[3] = x3;
+    V[0] = y0; V[1] = y1; V[2] = y2; V[3] = y3;
+}
+
+__device__ __forceinline__ void draw1_3(const Tab3& e, uint32_t B1, uint32_t h0c, uint32_t l0c,
+                                        const KParams& p, uint32_t (&W)[4]) {
+    uint32_t x0 = e.c0k ^ B1, x1 = e.c1, x2 = h0c ^ e.c2k, x3 = l0c;
+#pragma unroll
+    for (int rr = 3; rr < 10; ++rr) {
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo(PHILOX_M0, x0, hi0, lo0);
+        mulhilo(PHILOX_M1, x2, hi1, lo1);
+        x0 = hi1 ^ x1 ^ p.rk0[rr];
+        x1 = lo1;
+        x2 = hi0 ^ x3 ^ p.rk1[rr];
+        x3 = lo0;
+    }
+    W[0] = x0; W[1] = x1; W[2] = x2; W[3] = x3;
+}
+
+// classes from the six bond planes (unsatisfied = 1): n unsatisfied bonds as a
+// bit-sliced count (n2 n1 n0); need = n <= 2 among the valid replicas
+__device__ __forceinline__ void classes3(uint32_t P0, uint32_t P1, uint32_t P2, uint32_t P3,
+                                         uint32_t P4, uint32_t P5, uint32_t vmask, uint32_t& need,
+                                         uint32_t& c4, uint32_t& c8, uint32_t& c12) {
+    const uint32_t sa = P0 ^ P1 ^ P2, ca = (P0 & P1) | (P2 & (P0 ^ P1));
+    const uint32_t sb = P3 ^ P4 ^ P5, cb = (P3 & P4) | (P5 & (P3 ^ P4));
+    const uint32_t n0 = sa ^ sb, kc = sa & sb;
+    const uint32_t n1 = ca ^ cb ^ kc, n2 = (ca & cb) | (kc & (ca ^ cb));
+    need = ~n2 & ~(n1 & n0) & vmask;
+    c12 = ~(n0 | n1 | n2);
+    c8 = ~n2 & ~n1 & n0;
+    c4 = ~n2 & n1 & ~n0;
+}
+
+__device__ __forceinline__ void cmp8_3(uint32_t c4, uint32_t c8, uint32_t c12, const Tab3& e,
+                                       const Tab3& f, const uint32_t (&W)[4],
+                                       const uint32_t (&V)[4], uint32_t& b, uint32_t& eq) {
+    b = 0u;
+    eq = 0xFFFFFFFFu;
+#pragma unroll
+    for (int m = 3; m >= 0; --m) {
+        const uint32_t t = c4 * f.B0[m] + c8 * f.B1[m] + c12 * f.B2[m];
+        b = (~V[m] & t) | (~(V[m] ^ t) & b);
+        eq &= ~(V[m] ^ t);
+    }
+#pragma unroll
+    for (int m = 3; m >= 0; --m) {
+        const uint32_t t = c4 * e.B0[m] + c8 * e.B1[m] + c12 * e.B2[m];
+        b = (~W[m] & t) | (~(W[m] ^ t) & b);
+        eq &= ~(W[m] ^ t);
+    }
+}
+
+__device__ __forceinline__ void finish3(uint32_t c4, uint32_t c8, uint32_t c12, const Tab3* tab,
+                                        uint32_t B1, uint32_t h0c, uint32_t l0c,
+                                        const KParams& p, uint32_t& und, uint32_t& lt) {
+#pragma unroll 1
+    for (int g = 2; g < 8 && und; ++g) {
+        uint32_t W[4];
+        draw1_3(tab[g], B1, h0c, l0c, p, W);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const uint32_t t = c4 * tab[g].B0[m] + c8 * tab[g].B1[m] + c12 * tab[g].B2[m];
+            lt |= und & t & ~W[m];
+            und &= ~(W[m] ^ t);
+        }
+    }
+}
+
+// site-table entry: x = lattice word (group offset included) | group << 16,
+//                   y = Philox site index | faces << 16 (bit f: the site is on the
+//                   face x = 0, x = L-1, y = 0, y = L-1, z = 0, z = L-1)
+template <int L>
+__device__ __forceinline__ uint2 site_entry(int g, int s) {
+    using S = Shape3<L>;
+    const int x = s % L, y = (s / L) % L, z = s / (L * L);
+    const uint32_t faces = (x == 0 ? 1u : 0u) | (x == L - 1 ? 2u : 0u) | (y == 0 ? 4u : 0u) |
+                           (y == L - 1 ? 8u : 0u) | (z == 0 ? 16u : 0u) | (z == L - 1 ? 32u : 0u);
+    return make_uint2((uint32_t)(g * S::CELLS + S::cell(x, y, z)) | ((uint32_t)g << 16),
+                      (uint32_t)s | (faces << 16));
+}
+
+// store a flipped site and its halo copies
+template <int L>
+__device__ __forceinline__ void store_site(uint32_t* la, uint32_t v, uint32_t faces) {
+    constexpr int P = L + 2, P2 = P * P;
+    la[0] = v;
+    if (faces & 1u) la[L] = v;
+    if (faces & 2u) la[-L] = v;
+    if (faces & 4u) la[L * P] = v;
+    if (faces & 8u) la[-L * P] = v;
+    if (faces & 16u) la[L * P2] = v;
+    if (faces & 32u) la[-L * P2] = v;
+}
+
+template <int L, bool EA>
+__device__ __forceinline__ void bond_planes(const uint32_t* la, const uint4* jw, uint32_t s,
+                                            uint32_t w, uint32_t (&P)[6]) {
+    constexpr int PP = L + 2, P2 = PP * PP;
+    P[0] = w ^ la[1];
+    P[1] = w ^ la[-1];
+    P[2] = w ^ la[PP];
+    P[3] = w ^ la[-PP];
+    P[4] = w ^ la[P2];
+    P[5] = w ^ la[-P2];
+    if (EA) {
+        const uint4 a = jw[2 * s], b = jw[2 * s + 1];
+        P[0] ^= a.x;
+        P[1] ^= a.y;
+        P[2] ^= a.z;
+        P[3] ^= a.w;
+        P[4] ^= b.x;
+        P[5] ^= b.y;
+    }
+}
+
+template <int L, bool EA>
+__global__ void __launch_bounds__(NT3, 8) k_sweep3d(KParams p, const uint32_t* cta2run) {
+    using S = Shape3<L>;
+    constexpr int G = S::G, H = S::H, N = S::N, P = S::P, P2 = S::P2, NW = NT3 / 32;
+    constexpr int W = S::W, WP = S::WP;
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t* lat = smem;                                               // G halo lattices
+    uint2* stab = reinterpret_cast<uint2*>(smem + S::LAT_WORDS);       // 2 x TAB entries
+    uint4* jw = reinterpret_cast<uint4*>(stab + 2 * S::TAB);           // EA: 2 uint4 per site
+    uint4* qbase = jw + (EA ? 2 * N : 0);                              // NW x (QW + 32)
+    __shared__ __align__(16) Tab3 tabs[2][G][8];
+    __shared__ uint32_t sA2x[G], sVm[G];
+    __shared__ int32_t sU[G][32], sNup[G][32];
+    __shared__ unsigned long long sAcc;
+
+    const RunDesc& r = p.runs[cta2run[blockIdx.x]];
+    const DevState* st = r.st;
+    if (st->status != S_OK) return;
+    const int i = st->step + 1;
+    const uint32_t R = st->R_cur;
+    const uint32_t gfirst = (blockIdx.x - r.cta0) * G;   // the CTA's first group in its run
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t* src = r.spins[(i - 1) & 1];
+    uint32_t* dst = r.spins[i & 1];
+    uint4* queue = qbase + warp * (S::QW + 32);
+    const int qcap = (p.qcap_limit >= 0 && p.qcap_limit < S::QW) ? p.qcap_limit : S::QW;
+    const int qflush = qcap >= 32 ? qcap - 32 : 0;
+
+    // per-group Philox part and valid-replica masks
+    uint32_t B1k;
+    {
+        uint32_t h1a, l1a;
+        mulhilo(PHILOX_M1, (uint32_t)i, h1a, l1a);
+        B1k = l1a ^ p.rk0[1];
+    }
+    if (threadIdx.x < G) {
+        const uint32_t g = threadIdx.x;
+        const uint32_t base = (gfirst + g) * 32u;
+        const uint32_t nval = base < R ? min(32u, R - base) : 0u;
+        sVm[g] = nval == 32u ? 0xFFFFFFFFu : ((1u << nval) - 1u);
+        uint32_t h0a, l0a;
+        mulhilo(PHILOX_M0, r.grp0 + gfirst + g, h0a, l0a);
+        sA2x[g] = h0a ^ p.rk1[0];
+    }
+    for (int k = threadIdx.x; k < G * 32; k += NT3) {
+        sU[k >> 5][k & 31] = 0;
+        sNup[k >> 5][k & 31] = 0;
+    }
+    if (threadIdx.x == 0) sAcc = 0ull;
+    // families of the new slots
+    for (int k = threadIdx.x; k < G * 32; k += NT3) {
+        const uint32_t slot = (gfirst + (k >> 5)) * 32u + (k & 31);
+        if (slot < R) r.fam[i & 1][slot] = r.fam[(i - 1) & 1][r.anc[slot]];
+    }
+    // gather the parent rows of every group and transpose them into the multi-spin form
+    for (int k = warp; k < G * (WP / 4); k += NW) {
+        const int g = k / (WP / 4), c4 = k % (WP / 4);
+        const uint32_t slot = (gfirst + g) * 32u + lane;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (slot < R) v = reinterpret_cast<const uint4*>(src + (size_t)r.anc[slot] * r.Wp)[c4];
+        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int b = 4 * c4 + m;
+            if (b < W) {  // warp-uniform
+                const uint32_t t = transpose32(w4[m], lane);
+                const int s = 32 * b + lane;
+                if (s < N)
+                    lat[g * S::CELLS + S::cell(s % L, (s / L) % L, s / (L * L))] = t;
+            }
+        }
+    }
+    // site tables of the two colours, and the bond signs (EA)
+    for (int k = threadIdx.x; k < 2 * S::TAB; k += NT3) {
+        const int colour = k / S::TAB, e = k % S::TAB;
+        const int g = e / H, q = e % H;
+        const int s0 = 2 * q;
+        const int x0 = s0 % L, yz = s0 / L;
+        const int s = s0 + ((((yz % L) + (yz / L) + x0) & 1) != colour ? 1 : 0);
+        stab[k] = site_entry<L>(g, s);
+    }
+    if (EA) {
+        for (int s = threadIdx.x; s < N; s += NT3) {
+            const int x = s % L, y = (s / L) % L, z = s / (L * L);
+            const uint32_t js = r.jbits[s];
+            const uint32_t jxm = r.jbits[z * L * L + y * L + (x + L - 1) % L];
+            const uint32_t jym = r.jbits[z * L * L + ((y + L - 1) % L) * L + x];
+            const uint32_t jzm = r.jbits[((z + L - 1) % L) * L * L + y * L + x];
+            jw[2 * s] = make_uint4(0u - (js & 1u), 0u - (jxm & 1u), 0u - ((js >> 1) & 1u),
+                                   0u - ((jym >> 1) & 1u));
+            jw[2 * s + 1] = make_uint4(0u - ((js >> 2) & 1u), 0u - ((jzm >> 2) & 1u), 0u, 0u);
+        }
+    }
+    __syncthreads();
+    // periodic copies in the halo faces
+    for (int k = threadIdx.x; k < G * 6 * L * L; k += NT3) {
+        const int g = k / (6 * L * L), f = (k / (L * L)) % 6, a = k % L, b = (k / L) % L;
+        uint32_t* lg = lat + g * S::CELLS;
+        int d, sidx;
+        switch (f) {
+            case 0: d = S::cell(L, a, b); sidx = S::cell(0, a, b); break;
+            case 1: d = S::cell(-1, a, b); sidx = S::cell(L - 1, a, b); break;
+            case 2: d = S::cell(a, L, b); sidx = S::cell(a, 0, b); break;
+            case 3: d = S::cell(a, -1, b); sidx = S::cell(a, L - 1, b); break;
+            case 4: d = S::cell(a, b, L); sidx = S::cell(a, b, 0); break;
+            default: d = S::cell(a, b, -1); sidx = S::cell(a, b, L - 1); break;
+        }
+        lg[d] = lg[sidx];
+    }
+
+    const uint32_t nh = 2u * p.theta[i - 1];
+    const uint32_t* thr = p.thr + 4 * (i - 1);
+    if (nh > 0 && threadIdx.x < 8 * G)
+        build_tab3(tabs[0][threadIdx.x >> 3], threadIdx.x & 7, p, r.grp0 + gfirst + (threadIdx.x >> 3),
+                   (uint32_t)i, 0u, 0, thr);
+    __syncthreads();
+
+    const uint32_t lml = (1u << lane) - 1u;
+    uint32_t acc = 0;
+    for (uint32_t h = 0; h < nh; ++h) {
+        const int colour = (int)(h & 1u);
+        if (h + 1 < nh && threadIdx.x < 8 * G)
+            build_tab3(tabs[(h + 1) & 1u][threadIdx.x >> 3], threadIdx.x & 7, p,
+                       r.grp0 + gfirst + (threadIdx.x >> 3), (uint32_t)i, (h + 1) >> 1,
+                       (int)((h + 1) & 1u), thr);
+        const uint2* ct = stab + colour * S::TAB;
+        int k = 0;
+        while (true) {
+            int wq = 0;
+#pragma unroll 1
+            for (; k < S::ITERS && wq <= qflush; ++k) {
+                const int e = threadIdx.x + k * NT3;
+                const bool have = e < S::TAB;
+                // lanes past the table run entry 0 with no valid replica (no flip, no queue)
+                const uint2 en = ct[have ? e : 0];
+                const int g = (int)(en.x >> 16);
+                uint32_t* la = lat + (en.x & 0xFFFFu);
+                const uint32_t s = en.y & 0xFFFFu;
+                const uint32_t vm = have ? sVm[g] : 0u;
+                const uint32_t w = la[0];
+                uint32_t Pb[6];
+                bond_planes<L, EA>(la, jw, s, w, Pb);
+                uint32_t need, c4, c8, c12;
+                classes3(Pb[0], Pb[1], Pb[2], Pb[3], Pb[4], Pb[5], vm, need, c4, c8, c12);
+                const uint32_t A2s = sA2x[g] ^ s;
+                uint32_t B1, h0c, l0c;
+                {
+                    uint32_t h1b, l1b;
+                    mulhilo(PHILOX_M1, A2s, h1b, l1b);
+                    B1 = l1b;
+                    mulhilo(PHILOX_M0, h1b ^ B1k, h0c, l0c);
+                }
+                const Tab3* tb = tabs[h & 1u][g];
+                uint32_t Wd[4], Vd[4];
+                draw2_3(tb[0], tb[1], B1, h0c, l0c, p, Wd, Vd);
+                uint32_t b, eq;
+                cmp8_3(c4, c8, c12, tb[0], tb[1], Wd, Vd, b, eq);
+                const uint32_t lt = b & need;
+                const uint32_t und = eq & need;
+                const bool undecided = und != 0u;
+                const uint32_t ball = __ballot_sync(0xFFFFFFFFu, undecided);
+                const int slot = undecided ? wq + __popc(ball & lml) : S::QW + lane;
+                queue[slot] = make_uint4(A2s, und, lt, (uint32_t)e);
+                const uint32_t f = (~need | lt) & (undecided ? 0u : vm);
+                if (have) store_site<L>(la, w ^ f, en.y >> 16);
+                acc += (uint32_t)__popc(f);
+                wq += __popc(ball);
+            }
+            // the warp's undecided sites, one per lane, from plane block 2 on
+            __syncwarp();
+            for (int e2 = lane; e2 < wq; e2 += 32) {
+                const uint4 q = queue[e2];
+                const uint2 en = ct[q.w];
+                const int g = (int)(en.x >> 16);
+                uint32_t* la = lat + (en.x & 0xFFFFu);
+                const uint32_t s = en.y & 0xFFFFu;
+                const uint32_t vm = sVm[g];
+                const uint32_t w = la[0];
+                uint32_t Pb[6];
+                bond_planes<L, EA>(la, jw, s, w, Pb);
+                uint32_t need, c4, c8, c12;
+                classes3(Pb[0], Pb[1], Pb[2], Pb[3], Pb[4], Pb[5], vm, need, c4, c8, c12);
+                uint32_t B1, h0c, l0c;
+                {
+                    uint32_t h1b, l1b;
+                    mulhilo(PHILOX_M1, q.x, h1b, l1b);
+                    B1 = l1b;
+                    mulhilo(PHILOX_M0, h1b ^ B1k, h0c, l0c);
+                }
+                uint32_t und = q.y, lt = q.z;
+                finish3(c4, c8, c12, tabs[h & 1u][g], B1, h0c, l0c, p, und, lt);
+                const uint32_t f = (~need | lt) & vm;
+                store_site<L>(la, w ^ f, en.y >> 16);
+                acc += (uint32_t)__popc(f);
+            }
+            __syncwarp();
+            if (k == S::ITERS) break;
+        }
+        __syncthreads();
+    }
+
+    // measurement: unsatisfied bonds U and up-count per replica, write back
+    for (int k = warp; k < G * (WP / 4); k += NW) {
+        const int g = k / (WP / 4), c4 = k % (WP / 4);
+        const uint32_t* lg = lat + g * S::CELLS;
+        int32_t U = 0, nup = 0;
+        uint32_t out[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int b = 4 * c4 + m;
+            out[m] = 0u;
+            if (b < W) {  // warp-uniform
+                const int s = 32 * b + lane;
+                const bool in = s < N;
+                uint32_t w = 0u, P0 = 0u, P1 = 0u, P2v = 0u;
+                if (in) {
+                    const int c = S::cell(s % L, (s / L) % L, s / (L * L));
+                    w = lg[c];
+                    P0 = w ^ lg[c + 1];
+                    P1 = w ^ lg[c + P];
+                    P2v = w ^ lg[c + P2];
+                    if (EA) {
+                        const uint4 a = jw[2 * s], bb = jw[2 * s + 1];
+                        P0 ^= a.x;
+                        P1 ^= a.z;
+                        P2v ^= bb.x;
+                    }
+                }
+                const uint32_t tw = transpose32(w, lane);
+                out[m] = tw;
+                nup += __popc(tw);
+                U += __popc(transpose32(P0, lane)) + __popc(transpose32(P1, lane)) +
+                     __popc(transpose32(P2v, lane));
+            }
+        }
+        const uint32_t slot = (gfirst + g) * 32u + lane;
+        if (slot < R)
+            reinterpret_cast<uint4*>(dst + (size_t)slot * r.Wp)[c4] =
+                make_uint4(out[0], out[1], out[2], out[3]);
+        atomicAdd(&sU[g][lane], U);
+        atomicAdd(&sNup[g][lane], nup);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0 && acc) atomicAdd(&sAcc, (unsigned long long)acc);
+    __syncthreads();
+
+    for (int g = warp; g < G; g += NW) {
+        const uint32_t slot = (gfirst + g) * 32u + lane;
+        long long e = 0, e2 = 0, am = 0, m2 = 0;
+        if (slot < R) {
+            const int32_t Uv = sU[g][lane];
+            const int32_t E = 2 * Uv - 3 * N;
+            const int32_t M = N - 2 * sNup[g][lane];
+            r.E[i & 1][slot] = E;
+            r.M[slot] = M;
+            atomicAdd(&r.hist[Uv >> 1], 1u);
+            e = E;
+            e2 = (long long)E * E;
+            am = M < 0 ? -M : M;
+            m2 = (long long)M * M;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+            e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+            am += __shfl_xor_sync(0xffffffffu, am, o);
+            m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+        }
+        if (lane == 0 && (e | e2 | am | m2)) {
+            TraceRow* tr = r.trace + i;
+            atomicAdd(&tr->sumE, (unsigned long long)e);
+            atomicAdd(&tr->sumE2, (unsigned long long)e2);
+            atomicAdd(&tr->sumAbsM, (unsigned long long)am);
+            atomicAdd(&tr->sumM2, (unsigned long long)m2);
+        }
+    }
+    if (threadIdx.x == 0 && sAcc) atomicAdd(&r.trace[i].accepts, sAcc);
+}
+
+template <int L, bool EA>
+size_t smem3d() {
+    using S = Shape3<L>;
+    return (size_t)S::LAT_WORDS * 4 + (size_t)2 * S::TAB * 8 + (EA ? (size_t)S::N * 32 : 0) +
+           (size_t)(NT3 / 32) * (S::QW + 32) * 16;
+}
+
+template <int L, bool EA>
+cudaError_t launch3d(const KParams& p, const uint32_t* cta2run, uint32_t ncta, cudaStream_t s,
+                     bool attr_only) {
+    static bool attr_set = false;
+    const size_t sm = smem3d<L, EA>();
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep3d<L, EA>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (attr_only || ncta == 0) return cudaSuccess;
+    k_sweep3d<L, EA><<<ncta, NT3, sm, s>>>(p, cta2run);
+    return cudaGetLastError();
+}
+
+template <bool EA>
+cudaError_t launch3d_L(int L, const KParams& p, const uint32_t* cta2run, uint32_t ncta,
+                       cudaStream_t s, bool attr_only) {
+    switch (L) {
+        case 4: return launch3d<4, EA>(p, cta2run, ncta, s, attr_only);
+        case 6: return launch3d<6, EA>(p, cta2run, ncta, s, attr_only);
+        case 8: return launch3d<8, EA>(p, cta2run, ncta, s, attr_only);
+        case 10: return launch3d<10, EA>(p, cta2run, ncta, s, attr_only);
+        case 12: return launch3d<12, EA>(p, cta2run, ncta, s, attr_only);
+        case 14: return launch3d<14, EA>(p, cta2run, ncta, s, attr_only);
+        default: return launch3d<16, EA>(p, cta2run, ncta, s, attr_only);
+    }
+}
+
+}  // namespace
+
+// replica groups per CTA of the 3D kernel for side L (0: no 3D kernel for L)
+int sweep3d_groups(int L) {
+    switch (L) {
+        case 4: return Shape3<4>::G;
+        case 6: return Shape3<6>::G;
+        case 8: return Shape3<8>::G;
+        case 10: return Shape3<10>::G;
+        case 12: return Shape3<12>::G;
+        case 14: return Shape3<14>::G;
+        case 16: return Shape3<16>::G;
+        default: return 0;
+    }
+}
+
+// One launch of the 3D kernel over the CTAs of the runs of side L (cta2run: their
+// run indices, device memory).  attr_only: function attributes only (before a
+// stream capture).
+cudaError_t launch_sweep3d(const KParams& p, int L, const uint32_t* cta2run, uint32_t ncta,
+                           cudaStream_t s, bool attr_only) {
+    return p.ea ? launch3d_L<true>(L, p, cta2run, ncta, s, attr_only)
+                : launch3d_L<false>(L, p, cta2run, ncta, s, attr_only);
+}
+
+}  // namespace pa

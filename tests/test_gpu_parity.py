@@ -237,12 +237,14 @@ def test_sweep_launch_configuration_does_not_change_results(d, L, kind):
 @pytest.mark.parametrize("d,L,R,kind,method,bf,caps", [
     (2, 64, 96, "ferro", "systematic", 1.0, (0, 32)),
     (3, 6, 150, "ea", "poisson", 3.0, (0, 4)),
-    (3, 10, 40, "ea", "nearest", 2.0, (0, 16))])
+    (3, 10, 40, "ea", "nearest", 2.0, (0, 16)),
+    (2, 10, 60, "ea", "systematic", 1.5, (0, 4))])
 def test_sweep_queue_overflow_path(d, L, R, kind, method, bf, caps):
     """The sweep queues the sites still undecided after eight bits of the uniforms
     and finishes them in a second pass; a site that finds the queue full finishes
     at once.  With the queue capped (0: every such site finishes at once; a small
     cap: some of each) the run must still equal the oracle bit for bit at every
-    step: 2D Ising L=64 to beta 1, 3D +-J L=6 and L=10 to beta 2-3."""
+    step: 2D Ising L=64 to beta 1, 3D +-J L=6 and L=10 to beta 2-3, 2D +-J L=10 (the
+    general kernel of non-power-of-two 2D lattices)."""
     for cap in caps:
         run_parity(d, L, R, 6, bf, 3, method, 29 + cap, kind=kind, queue_cap=cap)
