@@ -392,7 +392,12 @@ pa_status pa_set_graph(pa_ctx *ctx, int32_t on);
  * Non-finite or out-of-range outputs, or use_mlp = 0, take the plain step
  * (plain_units, plain_theta).  When beta reaches beta[K] the run finishes:
  * later pa_step calls launch nothing useful and pa_sync reports PA_OK.
- * Only for single-run contexts, before the first pa_step. */
+ * In a batch every run takes its own steps (one controller CTA per run, the
+ * run's own step tables, the same network and settings); runs finish after
+ * different step counts, the context once all have finished (PA_ERR_DONE from
+ * pa_step), and the per-run calls report each run at its own step.  pa_weighted
+ * then returns PA_ERR_ARG (the runs' temperatures differ at a step index).
+ * Call before the first pa_step; not with partial resampling (PA_ERR_ARG). */
 #define PA_MLP_IN 8
 #define PA_MLP_HIDDEN 64
 #define PA_MLP_OUT 2
@@ -415,6 +420,9 @@ pa_status pa_set_controller(pa_ctx *ctx, const pa_controller *cfg);
  * values) and theta[0..step-1]; *n receives step + 1. */
 pa_status pa_schedule_taken(pa_ctx *ctx, double *beta, uint32_t *theta, int32_t max,
                             int32_t *n);
+/* The same for run `run` of a batch. */
+pa_status pa_run_schedule_taken(pa_ctx *ctx, int32_t run, double *beta, uint32_t *theta,
+                                int32_t max, int32_t *n);
 
 /* Training of the network on the device (stateless; all pointers device).
  * X [B][8] features, Yt [B][2] targets, mask [B][2] weights of the squared

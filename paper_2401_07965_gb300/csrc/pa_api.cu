@@ -38,7 +38,7 @@ struct RunHost {
 enum Region {
     R_SPIN0, R_SPIN1, R_E0, R_E1, R_F0, R_F1, R_M, R_ANC, R_CNT, R_C, R_G, R_HIST, R_FLEV, R_TREE,
     R_PA, R_PB, R_OA, R_OB, R_PD, R_PCL, R_W, R_WP, R_OP, R_JB, R_ST, R_TRACE, R_LB1, R_LB2,
-    R_TICK, R_COUNT
+    R_TICK, R_SB, R_SDB, R_SQ, R_STHR, R_STH, R_COUNT
 };
 
 enum Shared {
@@ -88,6 +88,11 @@ struct pa_ctx {
     uint32_t* d_ovtick = nullptr;           // and per-pair CTA tickets (zero between calls)
     std::vector<int32_t> pairs_cached;      // the pair list currently in d_pairs
     bool controlled = false;                // learned schedule active
+    std::vector<std::vector<double>> rbeta;     // learned schedule: each run's betas and
+    std::vector<std::vector<uint32_t>> rtheta;  // sweeps so far (host copies)
+    std::vector<int> rstep;                     // and its completed steps
+    std::vector<char> rdone;                    // beta_f reached
+    std::vector<std::array<size_t, 5>> rtab_off;  // offsets of its own step tables
     bool finished = false;                  // beta_f reached under the controller
     CtlDev* d_ctl = nullptr;
     double* d_gbeta = nullptr;
@@ -211,6 +216,11 @@ Layout make_layout(const std::vector<RunHost>& runs, int n_steps) {
         rs[R_TRACE] = (size_t)(n_steps + 1) * sizeof(TraceRow);
         rs[R_LB1] = rs[R_LB2] = (size_t)h.nblk * sizeof(LBDesc);
         rs[R_TICK] = 2 * sizeof(uint32_t);
+        // the run's own step tables (used under the learned schedule)
+        rs[R_SB] = (size_t)(n_steps + 1) * 8;
+        rs[R_SDB] = rs[R_SQ] = (size_t)n_steps * 8;
+        rs[R_STHR] = (size_t)n_steps * 16;
+        rs[R_STH] = (size_t)n_steps * 4;
         for (int r = 0; r < R_COUNT; ++r) {
             off[r] = o;
             o += align256(rs[r]);
@@ -316,7 +326,7 @@ void fill_obs(const pa_ctx* ctx, int run, const TraceRow& t, int step, pa_obs* o
     o->step = step;
     o->R_i = t.R_i;
     o->R_prev = t.R_prev;
-    o->beta = ctx->beta[step];
+    o->beta = ctx->controlled ? ctx->rbeta[run][step] : ctx->beta[step];
     o->lnQ = t.lnQ;
     o->sum_lnQ = t.sum_lnQ;
     o->sumE = (int64_t)t.sumE;
@@ -347,7 +357,9 @@ void fill_obs(const pa_ctx* ctx, int run, const TraceRow& t, int step, pa_obs* o
     o->c = o->beta * o->beta * N * (o->e2 - o->e * o->e);
     o->chi = o->beta * N * (o->m2 - o->absm * o->absm);
     o->rho_t = (double)o->sumC2 / R;
-    const double th = step > 0 ? (double)ctx->theta[step - 1] : 0.0;
+    const double th =
+        step > 0 ? (double)(ctx->controlled ? ctx->rtheta[run][step - 1] : ctx->theta[step - 1])
+                 : 0.0;
     o->accept_rate = th > 0 ? (double)o->accepts / (th * N * R) : 0.0;
     for (int k = 0; k < 8; ++k) o->features[k] = t.x[k];
     o->u_next = t.u_next;
@@ -380,11 +392,24 @@ void thresholds_at(double beta, uint32_t out[4]) {
 // copy the step tables written by the controller back to the host
 pa_status refresh_schedule(pa_ctx* ctx) {
     const int n = ctx->n_steps;
-    PA_CUDA(cudaMemcpy(ctx->beta.data(), ctx->kp.beta, sizeof(double) * (n + 1),
-                       cudaMemcpyDeviceToHost));
-    PA_CUDA(cudaMemcpy(ctx->theta.data(), ctx->kp.theta, sizeof(uint32_t) * n,
-                       cudaMemcpyDeviceToHost));
+    for (int m = 0; m < ctx->M; ++m) {
+        PA_CUDA(cudaMemcpy(ctx->rbeta[m].data(), ctx->desc[m].sbeta, sizeof(double) * (n + 1),
+                           cudaMemcpyDeviceToHost));
+        PA_CUDA(cudaMemcpy(ctx->rtheta[m].data(), ctx->desc[m].stheta, sizeof(uint32_t) * n,
+                           cudaMemcpyDeviceToHost));
+    }
     return PA_OK;
+}
+
+// completed steps of one run (runs of a controlled batch advance separately)
+int run_step(const pa_ctx* ctx, int run) {
+    return ctx->controlled ? ctx->rstep[run] : ctx->host_step;
+}
+double run_beta(const pa_ctx* ctx, int run, int i) {
+    return ctx->controlled ? ctx->rbeta[run][i] : ctx->beta[i];
+}
+uint32_t run_theta(const pa_ctx* ctx, int run, int i) {
+    return ctx->controlled ? ctx->rtheta[run][i] : ctx->theta[i];
 }
 
 // capture one temperature step; every kernel reads the step index and the
@@ -550,11 +575,6 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     ctx->d_pov = (double*)(base + lay.shared_off[S_POV]);
     ctx->d_ovacc = (uint32_t*)(base + lay.shared_off[S_OVACC]);
     ctx->d_ovtick = (uint32_t*)(base + lay.shared_off[S_OVTICK]);
-    p.beta_rw = (double*)p.beta;
-    p.dbeta_rw = (double*)p.dbeta;
-    p.q_rw = (double*)p.q;
-    p.thr_rw = (uint32_t*)p.thr;
-    p.theta_rw = (uint32_t*)p.theta;
     p.ctl = nullptr;
     p.alpha = -1.0;
     p.qcap_limit = -1;
@@ -622,6 +642,12 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
         r.jbits = (const uint8_t*)(base + off[R_JB]);
         r.st = (DevState*)(base + off[R_ST]);
         r.trace = (TraceRow*)(base + off[R_TRACE]);
+        r.sbeta = (double*)(base + lay.shared_off[S_BETA]);
+        r.sdbeta = (double*)(base + lay.shared_off[S_DBETA]);
+        r.sq = (double*)(base + lay.shared_off[S_Q]);
+        r.sthr = (uint32_t*)(base + lay.shared_off[S_THR]);
+        r.stheta = (uint32_t*)(base + lay.shared_off[S_THETA]);
+        ctx->rtab_off.push_back({off[R_SB], off[R_SDB], off[R_SQ], off[R_STHR], off[R_STH]});
         r.lb1 = (LBDesc*)(base + off[R_LB1]);
         r.lb2 = (LBDesc*)(base + off[R_LB2]);
         r.tick = (uint32_t*)(base + off[R_TICK]);
@@ -783,15 +809,20 @@ pa_status pa_sync(pa_ctx* ctx) {
     if (!ctx) return PA_ERR_ARG;
     if (ctx->sticky != PA_OK) return ctx->sticky;
     PA_CUDA(cudaStreamSynchronize(ctx->stream));
+    bool all_done = true;
+    int most = 0;
     for (int m = 0; m < ctx->M; ++m) {
         DevState st;
         PA_CUDA(cudaMemcpy(&st, ctx->desc[m].st, sizeof(DevState), cudaMemcpyDeviceToHost));
         if (ctx->controlled) {
-            ctx->host_step = st.step;
+            // runs of a controlled batch reach beta_f after different step counts
+            ctx->rstep[m] = st.step;
+            most = std::max(most, st.step);
             if (st.status == S_DONE) {
-                ctx->finished = true;
+                ctx->rdone[m] = 1;
                 st.status = S_OK;
             }
+            all_done = all_done && ctx->rdone[m];
         }
         const pa_status s = map_dev_status(st.status);
         if (s != PA_OK) {
@@ -799,7 +830,11 @@ pa_status pa_sync(pa_ctx* ctx) {
             return s;
         }
     }
-    if (ctx->controlled) return refresh_schedule(ctx);
+    if (ctx->controlled) {
+        ctx->host_step = most;
+        ctx->finished = all_done;
+        return refresh_schedule(ctx);
+    }
     return PA_OK;
 }
 
@@ -808,9 +843,9 @@ pa_status pa_run_observables(pa_ctx* ctx, int32_t run, pa_obs* out) {
     pa_status s = pa_sync(ctx);
     if (s != PA_OK) return s;
     TraceRow t;
-    PA_CUDA(cudaMemcpy(&t, ctx->desc[run].trace + ctx->host_step, sizeof(t),
-                       cudaMemcpyDeviceToHost));
-    fill_obs(ctx, run, t, ctx->host_step, out);
+    const int step = run_step(ctx, run);
+    PA_CUDA(cudaMemcpy(&t, ctx->desc[run].trace + step, sizeof(t), cudaMemcpyDeviceToHost));
+    fill_obs(ctx, run, t, step, out);
     return PA_OK;
 }
 
@@ -821,7 +856,7 @@ pa_status pa_run_trace(pa_ctx* ctx, int32_t run, pa_obs* rows, int32_t max_rows,
     if (!valid_run(ctx, run) || !rows || max_rows < 0) return PA_ERR_ARG;
     pa_status s = pa_sync(ctx);
     if (s != PA_OK) return s;
-    int n = ctx->host_step + 1;
+    int n = run_step(ctx, run) + 1;
     if (n > max_rows) n = max_rows;
     std::vector<TraceRow> t((size_t)n);
     if (n > 0)
@@ -845,7 +880,7 @@ pa_status pa_run_free_energy(pa_ctx* ctx, int32_t run, double* minus_beta_F, dou
     if (s != PA_OK) return s;
     const double N = ctx->runs[run].N;
     const double mbf = N * std::log(2.0) + st.sum_lnQ;
-    const double b = ctx->beta[ctx->host_step];
+    const double b = run_beta(ctx, run, run_step(ctx, run));
     if (minus_beta_F) *minus_beta_F = mbf;
     if (f_per_spin) *f_per_spin = b > 0 ? -mbf / (b * N) : NAN;
     return PA_OK;
@@ -863,7 +898,7 @@ pa_status pa_run_get_array(pa_ctx* ctx, int32_t run, pa_array which, void* host,
     DevState st;
     s = read_state(ctx, run, &st);
     if (s != PA_OK) return s;
-    const int par = ctx->host_step & 1;
+    const int par = run_step(ctx, run) & 1;
     const RunDesc& r = ctx->desc[run];
     const RunHost& h = ctx->runs[run];
     size_t n = 0;
@@ -889,7 +924,7 @@ pa_status pa_run_get_array(pa_ctx* ctx, int32_t run, pa_array which, void* host,
             break;
         }
         case PA_ARRAY_COUNTS:
-            n = ctx->host_step > 0 ? st.R_prev : 0;
+            n = run_step(ctx, run) > 0 ? st.R_prev : 0;
             if (capacity < n) return PA_ERR_ARG;
             if (n) PA_CUDA(cudaMemcpy(host, r.counts, n * 4, cudaMemcpyDeviceToHost));
             break;
@@ -957,6 +992,8 @@ pa_status pa_set_state(pa_ctx* ctx, const uint32_t* spins, const uint32_t* famil
 pa_status pa_weighted(pa_ctx* ctx, int32_t ensemble, pa_weighted_obs* rows, int32_t max_rows,
                       int32_t* n_rows) {
     if (!ctx || !rows || max_rows < 0) return PA_ERR_ARG;
+    // under the learned schedule the runs' temperatures differ at a step index
+    if (ctx->controlled && ctx->M > 1) return PA_ERR_ARG;
     std::vector<int32_t> ids;
     for (int m = 0; m < ctx->M; ++m)
         if (ctx->runs[m].ensemble == ensemble) ids.push_back(m);
@@ -1014,7 +1051,8 @@ pa_status pa_overlap(pa_ctx* ctx, const int32_t* run_a, const int32_t* run_b, in
 }
 
 pa_status pa_set_partial_resampling(pa_ctx* ctx, double alpha) {
-    if (!ctx || ctx->host_step != 0 || ctx->kp.alpha >= 0.0 || !(alpha >= 0.0 && alpha <= 1.0))
+    if (!ctx || ctx->host_step != 0 || ctx->kp.alpha >= 0.0 || ctx->controlled ||
+        !(alpha >= 0.0 && alpha <= 1.0))
         return PA_ERR_ARG;
     if (ctx->sticky != PA_OK) return PA_ERR_STATE;
     for (const RunHost& h : ctx->runs)
@@ -1044,7 +1082,8 @@ pa_status pa_set_partial_resampling(pa_ctx* ctx, double alpha) {
 }
 
 pa_status pa_set_controller(pa_ctx* ctx, const pa_controller* cfg) {
-    if (!ctx || !cfg || ctx->M != 1 || ctx->host_step != 0 || ctx->controlled) return PA_ERR_ARG;
+    if (!ctx || !cfg || ctx->host_step != 0 || ctx->controlled || ctx->kp.alpha >= 0.0)
+        return PA_ERR_ARG;
     if (ctx->sticky != PA_OK) return PA_ERR_STATE;
     const int K = ctx->n_steps;
     if (cfg->u_max < 1 || cfg->u_max > CTL_UMAX || cfg->plain_units < 1 ||
@@ -1088,6 +1127,34 @@ pa_status pa_set_controller(pa_ctx* ctx, const pa_controller* cfg) {
     PA_CUDA(cudaMemcpy(ctx->d_gthr, gthr.data(), gthr.size() * 4, cudaMemcpyHostToDevice));
     PA_CUDA(cudaMemcpy(ctx->d_gdb, gdb.data(), gdb.size() * 8, cudaMemcpyHostToDevice));
     PA_CUDA(cudaMemcpy(ctx->d_gq, gq.data(), gq.size() * 8, cudaMemcpyHostToDevice));
+    // every run gets its own step tables, initialised from the shared ones, which the
+    // controller then writes step by step
+    char* base = (char*)ctx->ws;
+    for (int m = 0; m < ctx->M; ++m) {
+        RunDesc& r = ctx->desc[m];
+        const auto& o = ctx->rtab_off[m];
+        double* sb = (double*)(base + o[0]);
+        double* sdb = (double*)(base + o[1]);
+        double* sq = (double*)(base + o[2]);
+        uint32_t* sthr = (uint32_t*)(base + o[3]);
+        uint32_t* sth = (uint32_t*)(base + o[4]);
+        PA_CUDA(cudaMemcpy(sb, ctx->kp.beta, sizeof(double) * (K + 1), cudaMemcpyDeviceToDevice));
+        PA_CUDA(cudaMemcpy(sdb, ctx->kp.dbeta, sizeof(double) * K, cudaMemcpyDeviceToDevice));
+        PA_CUDA(cudaMemcpy(sq, ctx->kp.q, sizeof(double) * K, cudaMemcpyDeviceToDevice));
+        PA_CUDA(cudaMemcpy(sthr, ctx->kp.thr, sizeof(uint32_t) * 4 * K, cudaMemcpyDeviceToDevice));
+        PA_CUDA(cudaMemcpy(sth, ctx->kp.theta, sizeof(uint32_t) * K, cudaMemcpyDeviceToDevice));
+        r.sbeta = sb;
+        r.sdbeta = sdb;
+        r.sq = sq;
+        r.sthr = sthr;
+        r.stheta = sth;
+    }
+    PA_CUDA(cudaMemcpy((void*)ctx->kp.runs, ctx->desc.data(), sizeof(RunDesc) * ctx->M,
+                       cudaMemcpyHostToDevice));
+    ctx->rbeta.assign(ctx->M, ctx->beta);
+    ctx->rtheta.assign(ctx->M, ctx->theta);
+    ctx->rstep.assign(ctx->M, 0);
+    ctx->rdone.assign(ctx->M, 0);
     ctx->kp.ctl = ctx->d_ctl;
     ctx->controlled = true;
     if (ctx->graph) {  // the step graph must now include the controller
@@ -1100,19 +1167,24 @@ pa_status pa_set_controller(pa_ctx* ctx, const pa_controller* cfg) {
     return pa_sync(ctx);
 }
 
-pa_status pa_schedule_taken(pa_ctx* ctx, double* beta, uint32_t* theta, int32_t max,
-                            int32_t* n) {
-    if (!ctx || max < 0) return PA_ERR_ARG;
+pa_status pa_run_schedule_taken(pa_ctx* ctx, int32_t run, double* beta, uint32_t* theta,
+                                int32_t max, int32_t* n) {
+    if (!valid_run(ctx, run) || max < 0) return PA_ERR_ARG;
     pa_status s = pa_sync(ctx);
     if (s != PA_OK) return s;
-    int cnt = ctx->host_step + 1;
+    int cnt = run_step(ctx, run) + 1;
     if (cnt > max) cnt = max;
     for (int i = 0; i < cnt; ++i) {
-        if (beta) beta[i] = ctx->beta[i];
-        if (theta && i > 0) theta[i - 1] = ctx->theta[i - 1];
+        if (beta) beta[i] = run_beta(ctx, run, i);
+        if (theta && i > 0) theta[i - 1] = run_theta(ctx, run, i - 1);
     }
     if (n) *n = cnt;
     return PA_OK;
+}
+
+pa_status pa_schedule_taken(pa_ctx* ctx, double* beta, uint32_t* theta, int32_t max,
+                            int32_t* n) {
+    return pa_run_schedule_taken(ctx, 0, beta, theta, max, n);
 }
 
 pa_status pa_set_graph(pa_ctx* ctx, int32_t on) {
@@ -1149,7 +1221,7 @@ pa_status pa_sweep_timing(pa_ctx* ctx, double* ms, int64_t* launches, double* up
         total += f;
         const int i = ctx->timed_steps[k];
         for (int m = 0; m < ctx->M; ++m)
-            upd += (double)ctx->theta[i - 1] * (double)ctx->runs[m].N * (double)t[m][i].R_i;
+            upd += (double)run_theta(ctx, m, i - 1) * (double)ctx->runs[m].N * (double)t[m][i].R_i;
     }
     if (ms) *ms = total;
     if (launches) *launches = (int64_t)ctx->ev_used;

@@ -44,7 +44,7 @@ __device__ __forceinline__ float bf_round(float v) {
 // controller step
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(64) k_control(KParams p) {
-    const RunDesc& r = p.runs[0];
+    const RunDesc& r = p.runs[blockIdx.x];  // one CTA per run of the batch
     DevState* st = r.st;
     if (st->status != S_OK) return;
     const CtlDev& c = *p.ctl;
@@ -56,9 +56,9 @@ __global__ void __launch_bounds__(64) k_control(KParams p) {
         const double R = (double)tr->R_i, N = (double)r.N;
         const double mE = (double)(long long)tr->sumE / R;
         const double var = ((double)(long long)tr->sumE2 / R - mE * mE) / N;
-        const double th = i > 0 ? (double)p.theta[i - 1] : 0.0;
+        const double th = i > 0 ? (double)r.stheta[i - 1] : 0.0;
         const double lnR0 = log(fmax((double)r.R, 2.0));
-        x[0] = (float)p.beta[i];
+        x[0] = (float)r.sbeta[i];
         x[1] = (float)(mE / N);
         x[2] = (float)(var / 10.0);
         x[3] = (float)(tr->lnQ / N * 10.0);
@@ -122,11 +122,11 @@ __global__ void __launch_bounds__(64) k_control(KParams p) {
         if ((long long)th > cap) th = cap > (long long)c.theta_min ? (uint32_t)cap : c.theta_min;
     }
     const int kn = k + u;
-    p.beta_rw[i + 1] = c.beta_grid[kn];
-    p.dbeta_rw[i] = c.dbeta_tab[(size_t)k * CTL_UMAX + (u - 1)];
-    p.q_rw[i] = c.q_tab[(size_t)k * CTL_UMAX + (u - 1)];
-    for (int m = 0; m < 4; ++m) p.thr_rw[4 * i + m] = c.thr_grid[4 * kn + m];
-    p.theta_rw[i] = th;
+    r.sbeta[i + 1] = c.beta_grid[kn];
+    r.sdbeta[i] = c.dbeta_tab[(size_t)k * CTL_UMAX + (u - 1)];
+    r.sq[i] = c.q_tab[(size_t)k * CTL_UMAX + (u - 1)];
+    for (int m = 0; m < 4; ++m) r.sthr[4 * i + m] = c.thr_grid[4 * kn + m];
+    r.stheta[i] = th;
     st->kgrid = kn;
     st->sweeps = used + th;
     tr->u_next = u;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(64) k_control(KParams p) {
 }
 
 cudaError_t launch_control(const KParams& p, cudaStream_t s) {
-    k_control<<<1, 64, 0, s>>>(p);
+    k_control<<<p.M, 64, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -182,6 +182,13 @@ struct RunDesc {
     const uint8_t* jbits;    // bit a of byte s: bond (s, s+e_a) has J = -1
     DevState* st;
     TraceRow* trace;         // n_steps + 1 rows
+    // the run's step tables (beta_i, dbeta_i, q_i, thresholds, theta_i): the batch's
+    // shared tables, or the run's own under the learned schedule
+    double* sbeta;
+    double* sdbeta;
+    double* sq;
+    uint32_t* sthr;
+    uint32_t* stheta;
     LBDesc* lb1;             // look-back descriptors: prefix of the expected copies
     LBDesc* lb2;             // and of the copy numbers
     uint32_t* tick;          // [0] scan-block tickets, [1] family-block tickets
@@ -203,11 +210,6 @@ struct KParams {
     const double* q;         // exp(-4 dbeta), n_steps
     const uint32_t* thr;     // 4 per step (index 1..d used)
     const uint32_t* theta;   // n_steps
-    double* beta_rw;         // the same tables, written by the learned-schedule controller
-    double* dbeta_rw;
-    double* q_rw;
-    uint32_t* thr_rw;
-    uint32_t* theta_rw;
     const CtlDev* ctl;       // null without a controller
     double alpha;            // partial resampling threshold (< 0: resample every step)
     int qcap_limit;          // sweep: cap on the undecided-site queue (< 0: its full size)

@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
     const int K = hi - lo + 1;
     int P = 1;
     while (P < K) P <<= 1;
-    const double q = p.q[i - 1];
+    const double q = r.sq[i - 1];
     if (p.alpha >= 0.0) {
         // partial resampling: the level factors q^k; k_pw_final closes the step
         double* wl = reinterpret_cast<double*>(r.flev);
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
         const int32_t Umin = 2 * lmin + r.parity;
         const int32_t Emin = 2 * Umin - p.d * r.N;
         const double lnQ = __dsub_rn(__dsub_rn(log(S), log((double)Rprev)),
-                                     __dmul_rn(p.dbeta[i - 1], (double)Emin));
+                                     __dmul_rn(r.sdbeta[i - 1], (double)Emin));
         st->R_prev = Rprev;
         st->lmin = (uint32_t)lmin;
         st->K = (uint32_t)K;
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(1024) k_pw_final(KParams p) {
         const int32_t Umin = 2 * (int32_t)st->lmin + r.parity;
         const int32_t Emin = 2 * Umin - p.d * r.N;
         const double lnQ = __dsub_rn(__dsub_rn(log(S[1]), log(S[0])),
-                                     __dmul_rn(p.dbeta[i - 1], (double)Emin));
+                                     __dmul_rn(r.sdbeta[i - 1], (double)Emin));
         const double ess = __ddiv_rn(__dmul_rn(S[1], S[1]), S[2]);
         const int res = ess < __dmul_rn(p.alpha, (double)Rprev) ? 1 : 0;
         int e = 0;

@@ -265,10 +265,10 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
 
     uint32_t acc = 0;
     if (mode == 0) {
-        const uint32_t theta = p.theta[i - 1];
+        const uint32_t theta = r.stheta[i - 1];
         uint32_t thr[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) thr[k] = p.thr[4 * (i - 1) + k];
+        for (int k = 0; k < 4; ++k) thr[k] = r.sthr[4 * (i - 1) + k];
         const uint32_t grp = blockIdx.x;         // global replica group
         uint32_t h0a, l0a, h1a, l1a;
         mulhilo(PHILOX_M0, grp, h0a, l0a);

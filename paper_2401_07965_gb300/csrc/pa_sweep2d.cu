@@ -365,10 +365,10 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_sweep2d(KParams p) {
         A2x = h0a ^ p.rk1[0];
         B1k = l1a ^ p.rk0[1];
     }
-    const uint32_t nh = 2u * p.theta[i - 1];
+    const uint32_t nh = 2u * r.stheta[i - 1];
     if (nh > 0 && threadIdx.x < 8)
-        build_tab2(tabs[0], threadIdx.x, p, grp, (uint32_t)i, 0u, 0, p.thr[4 * (i - 1) + 1],
-                   p.thr[4 * (i - 1) + 2]);
+        build_tab2(tabs[0], threadIdx.x, p, grp, (uint32_t)i, 0u, 0, r.sthr[4 * (i - 1) + 1],
+                   r.sthr[4 * (i - 1) + 2]);
     __syncthreads();
 
     uint32_t acc = 0;
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_sweep2d(KParams p) {
         if (h + 1 < nh && threadIdx.x < 8) {
             const int ii = st->step + 1;
             build_tab2(tabs[(h + 1) & 1u], threadIdx.x, p, grp, (uint32_t)ii, (h + 1) >> 1,
-                       (int)((h + 1) & 1u), p.thr[4 * (ii - 1) + 1], p.thr[4 * (ii - 1) + 2]);
+                       (int)((h + 1) & 1u), r.sthr[4 * (ii - 1) + 1], r.sthr[4 * (ii - 1) + 2]);
         }
         // the thread's place in the walk: column slot xi of rows y0, y0 + RP, ...
         int y0, xi;

@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(NT3, 8) k_sweep3d(KParams p, const uint32_t* c
         lg[d] = lg[sidx];
     }
 
-    const uint32_t nh = 2u * p.theta[i - 1];
-    const uint32_t* thr = p.thr + 4 * (i - 1);
+    const uint32_t nh = 2u * r.stheta[i - 1];
+    const uint32_t* thr = r.sthr + 4 * (i - 1);
     if (nh > 0 && threadIdx.x < 8 * G)
         build_tab3(tabs[0][threadIdx.x >> 3], threadIdx.x & 7, p, r.grp0 + gfirst + (threadIdx.x >> 3),
                    (uint32_t)i, 0u, 0, thr);

@@ -35,7 +35,8 @@ EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observable
            "pa_run_trace", "pa_run_free_energy", "pa_run_get_array", "pa_weighted",
            "pa_set_graph", "pa_set_controller", "pa_schedule_taken", "pa_mlp_scratch_bytes",
            "pa_mlp_forward", "pa_mlp_gradients", "pa_mlp_adam", "pa_overlap",
-           "pa_set_partial_resampling", "pa_weighted_rows", "pa_set_sweep_queue"]
+           "pa_set_partial_resampling", "pa_weighted_rows", "pa_set_sweep_queue",
+           "pa_run_schedule_taken"]
 
 
 class pa_lattice(C.Structure):
@@ -163,6 +164,8 @@ def _load():
     lib.pa_set_controller.argtypes = [vp, C.POINTER(pa_controller)]
     lib.pa_schedule_taken.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_uint32),
                                       C.c_int32, C.POINTER(C.c_int32)]
+    lib.pa_run_schedule_taken.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_uint32), C.c_int32, C.POINTER(C.c_int32)]
     lib.pa_mlp_scratch_bytes.argtypes = [C.c_int32]
     lib.pa_mlp_scratch_bytes.restype = sz
     lib.pa_mlp_forward.argtypes = [vp, vp, C.c_int32, vp, vp]
@@ -452,6 +455,16 @@ def pa_schedule_taken(ctx, max_rows):
     _check(_lib.pa_schedule_taken(ctx, b.ctypes.data_as(C.POINTER(C.c_double)),
                                   t.ctypes.data_as(C.POINTER(C.c_uint32)), max_rows, C.byref(n)),
            "pa_schedule_taken")
+    return b[: n.value], t[: max(n.value - 1, 0)]
+
+
+def pa_run_schedule_taken(ctx, run, max_rows):
+    b = np.zeros(max_rows, np.float64)
+    t = np.zeros(max(max_rows - 1, 1), np.uint32)
+    n = C.c_int32()
+    _check(_lib.pa_run_schedule_taken(ctx, int(run), b.ctypes.data_as(C.POINTER(C.c_double)),
+                                      t.ctypes.data_as(C.POINTER(C.c_uint32)), max_rows,
+                                      C.byref(n)), "pa_run_schedule_taken")
     return b[: n.value], t[: max(n.value - 1, 0)]
 
 

@@ -273,3 +273,62 @@ def test_controlled_run_under_graph_replay_equals_direct_launches():
     assert a.observables()["sum_lnQ"] == b.observables()["sum_lnQ"]
     a.close()
     b.close()
+
+
+def test_controlled_batch_each_run_replays_through_oracle():
+    """The learned schedule in a batch: every run takes its own steps (one controller
+    CTA per run).  For each run, every decision replays through the oracle's decision
+    rule from the recorded features, and the run's realized schedule rerun through the
+    oracle PA (with the run's replica-slot base and index) is bit-exact."""
+    K, units, theta = 120, 2, 6
+    bits = _test_params()
+    runs = [{"dim": 2, "L": 16, "R": 300}, {"dim": 2, "L": 16, "R": 200},
+            {"dim": 2, "L": 8, "R": 150}]
+    grid = np.linspace(0.0, 1.0, K + 1)
+    b = pa.Batch(runs, grid, np.full(K, theta, np.uint32), "nearest", 21)
+    pa.pa_set_controller(b.ctx, bits, 1, units, theta, 2, 40, 0, 8)
+    done = False
+    for _ in range(K // 8 + 2):  # at most one step per grid point
+        try:
+            b.step(8)
+        except pa.PAError as e:
+            assert e.status == pa.PA_ERR_DONE
+            done = True
+            break
+        pa.pa_sync(b.ctx)
+    assert done
+    budget = theta * (K // units)
+    cfg = dict(K=K, use_mlp=1, plain_units=units, plain_theta=theta, theta_min=2, theta_max=40,
+               budget=budget, u_max=8, theta_c=np.float32(budget) / np.float32(K // units))
+    schedules = []
+    for m, (spec, base) in enumerate(zip(b.specs, b.slot_bases())):
+        betas, thetas = pa.pa_run_schedule_taken(b.ctx, m, K + 1)
+        rows = b.trace(m)
+        n = len(betas) - 1
+        assert abs(betas[-1] - 1.0) < 1e-15 and len(rows) == n + 1
+        k, used = 0, 0
+        for i in range(n):
+            d = M.decide(M.forward32(bits, np.array(rows[i]["features"], np.float32)), k, used,
+                         cfg)
+            assert d == (rows[i]["u_next"], rows[i]["theta_next"]), (m, i)
+            k += d[0]
+            used += d[1]
+            assert betas[i + 1] == grid[k] and thetas[i] == d[1]
+        assert k == K
+        L, R = spec["L"], spec["R"]
+        cap = pa.default_capacity(R, "nearest")
+        orc = O.Run(2, L, O.ferro_couplings(2, L), R, betas, thetas, O.RESAMPLERS["nearest"], 21,
+                    R_cap=cap, slot_base=base, run_id=m)
+        for _ in range(n):
+            assert orc.step() == 0
+        g, o = b.observables(m), orc.obs()
+        assert g["R_i"] == o["R_i"] and g["step"] == n
+        for key in ("sumE", "sumE2", "sumAbsM", "sumM2", "sumC2", "accepts"):
+            assert g[key] == o[key], (m, key)
+        assert math.isclose(g["sum_lnQ"], o["sum_lnQ"], rel_tol=1e-12, abs_tol=1e-13)
+        assert np.array_equal(b.spins_words(m), O.pack_spins(orc.spins())), m
+        schedules.append(tuple(betas))
+    assert len(set(schedules)) > 1  # the runs took different schedules
+    with pytest.raises(pa.PAError):
+        b.weighted(0)
+    b.close()
