@@ -273,7 +273,7 @@ __device__ __forceinline__ void site_pass2(uint32_t* lat, const uint4* jw, const
 }
 
 template <int L, int NT, bool EA>
-__global__ void __launch_bounds__(NT, 65536 / (NT * 64)) k_sweep2d(KParams p) {
+__global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
     constexpr int P = L + 2, N = L * L, TPR = L / 2, RP = NT / TPR, ITERS = L / RP;
     constexpr int NW = NT / 32, W = N / 32;
     constexpr int LG = (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6 : 7;
