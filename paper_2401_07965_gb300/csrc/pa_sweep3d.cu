@@ -4,18 +4,28 @@
 // small lattices.  Random numbers, decisions and results are the same.
 //
 // Grouping.  A 3D lattice of a few hundred sites gives one group of 32 replicas
-// too little work per half-sweep (and per barrier), so a CTA of 128 threads
-// holds G replica groups of one run (G = 8, 4, 2, 1 for L = 4, 6, 8, >= 10):
-// G halo-padded multi-spin lattices in shared memory (cell (x, y, z),
-// -1 <= x, y, z <= L, word ((z+1)(L+2) + y+1)(L+2) + x+1), each group keeping
-// its own Philox counter (its global replica group).  Every neighbour of an
-// interior site is at a fixed offset +-1, +-(L+2), +-(L+2)^2; a flip of a
-// boundary site also writes its copies in the halo faces.
+// too little work per half-sweep (and per barrier, and per flush of the queue
+// of undecided sites), so a CTA of 128 threads holds G replica groups of one
+// run (G = 16, 8, 4, 2 for L = 4, 6, 8, 10; 1 above), about eight site words
+// per thread and half-sweep: G halo-padded multi-spin lattices in shared
+// memory (cell (x, y, z), -1 <= x, y, z <= L, word ((z+1)(L+2) + y+1)(L+2) +
+// x+1), each group keeping its own Philox counter (its global replica group).
+// Every neighbour of an interior site is at a fixed offset +-1, +-(L+2),
+// +-(L+2)^2; a flip of a boundary site also writes its copies in the halo faces.
 //
-// Walk.  A per-colour table lists the G x N/2 sites of the colour (lattice
-// word, group, Philox site index, boundary faces); thread t takes entries
-// t, t + 128, ...  Undecided sites after eight planes go to per-warp queues
-// and are finished by the same warp (branch-free first pass, as in 2D).
+// Walk.  A per-colour table lists the N/2 sites of the colour (lattice word,
+// boundary faces, Philox site index) and, for the spin glass, the six bond
+// signs of each as byte sign bits; entry e of the CTA's G x N/2 work items is
+// group e / (N/2), site e mod (N/2), thread t taking e = t, t + 128, ...
+// Consecutive lanes read consecutive table words.  Undecided sites after eight
+// planes go to per-warp queues and are finished by the same warp (branch-free
+// first pass, as in 2D).
+//
+// Philox.  Of the round-2 and round-3 values that do not depend on the site,
+// the part that does not depend on the group either (the counter word holding
+// sweep, colour and plane block) is computed once per half-sweep and plane
+// block; the group's part of blocks 0 and 1 is tabulated per group; blocks 2-7,
+// needed by few sites, are completed in the queue pass.
 //
 // Energy classes of d = 3 (n unsatisfied bonds of 6): dE = 4 (n = 2), 8 (n = 1),
 // 12 (n = 0), disjoint masks, so a plane's threshold bit word is the sum
@@ -27,59 +37,50 @@ namespace {
 
 constexpr int NT3 = 128;
 
+// replica groups per CTA of side L
+template <int L>
+struct Groups3 {
+    static constexpr int value = L == 4 ? 16 : (L == 6 ? 8 : (L == 8 ? 4 : (L == 10 ? 2 : 1)));
+};
+
 template <int L>
 struct Shape3 {
     static constexpr int P = L + 2, P2 = P * P, N = L * L * L, H = N / 2;
-    static constexpr int G = (4 * NT3) / H >= 8 ? 8 : ((4 * NT3) / H >= 1 ? (4 * NT3) / H : 1);
+    static constexpr int G = Groups3<L>::value;
     static constexpr int ITERS = (G * H + NT3 - 1) / NT3;
     static constexpr int W = (N + 31) / 32, WP = (W + 3) & ~3;
     static constexpr int CELLS = P * P * P;
     static constexpr int LAT_WORDS = (G * CELLS + 3) & ~3;
-    static constexpr int QW = (32 * ITERS) / 4 + 32;          // per warp, then 32 scratch slots
-    static constexpr int TAB = G * H;                         // table entries per colour
+    // per warp, then 32 scratch slots
+    static constexpr int QW = ((32 * ITERS) / 4 < 64 ? (32 * ITERS) / 4 : 64) + 32;
     __host__ __device__ static constexpr int cell(int x, int y, int z) {
         return ((z + 1) * P + y + 1) * P + x + 1;
     }
 };
 
-// Philox table of one plane block (site-independent round-3 values) and the
-// threshold bits (0/1) of its planes for dE = 4, 8, 12
-struct Tab3 {
-    uint32_t c0k, c1, c2k, pad;
-    uint32_t B0[4], B1[4], B2[4];
-};
-
-__device__ __forceinline__ void build_tab3(Tab3* tab, int g, const KParams& p, uint32_t grp,
-                                           uint32_t step, uint32_t t, int colour,
-                                           const uint32_t* thr) {
-    uint32_t h0a, l0a, h1a, l1a, h0b, l0b, h1c, l1c;
-    mulhilo(PHILOX_M0, grp, h0a, l0a);
-    mulhilo(PHILOX_M1, step, h1a, l1a);
-    const uint32_t c1v = DOM_SWEEP | (t << 4) | ((uint32_t)colour << 3) | (uint32_t)g;
-    const uint32_t A0 = h1a ^ c1v ^ p.rk0[0];
-    mulhilo(PHILOX_M0, A0, h0b, l0b);
-    const uint32_t B2 = h0b ^ l0a ^ p.rk1[1];
-    mulhilo(PHILOX_M1, B2, h1c, l1c);
-    Tab3 e;
-    e.c0k = h1c ^ p.rk0[2];
-    e.c1 = l1c;
-    e.c2k = l0b ^ p.rk1[2];
-    e.pad = 0u;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const int sh = 31 - (4 * g + m);
-        e.B0[m] = (thr[1] >> sh) & 1u;
-        e.B1[m] = (thr[2] >> sh) & 1u;
-        e.B2[m] = (thr[3] >> sh) & 1u;
-    }
-    tab[g] = e;
+// The group-independent round-2 product of a plane block's counter word
+// (DOM_SWEEP | sweep << 4 | colour << 3 | block) and the key: (h0b, c2k).
+__device__ __forceinline__ uint2 block_part(const KParams& p, uint32_t h1a, uint32_t t, int colour,
+                                            int b) {
+    const uint32_t c1v = DOM_SWEEP | (t << 4) | ((uint32_t)colour << 3) | (uint32_t)b;
+    uint32_t h0b, l0b;
+    mulhilo(PHILOX_M0, h1a ^ c1v ^ p.rk0[0], h0b, l0b);
+    return make_uint2(h0b, l0b ^ p.rk1[2]);
 }
 
-__device__ __forceinline__ void draw2_3(const Tab3& e, const Tab3& f, uint32_t B1, uint32_t h0c,
+// a group's round-3 values of a plane block (c0k, c1, c2k): l0a is the low word
+// of the group counter's round-1 product
+__device__ __forceinline__ uint4 group_part(const KParams& p, uint2 bp, uint32_t l0a) {
+    uint32_t h1c, l1c;
+    mulhilo(PHILOX_M1, bp.x ^ l0a ^ p.rk1[1], h1c, l1c);
+    return make_uint4(h1c ^ p.rk0[2], l1c, bp.y, 0u);
+}
+
+__device__ __forceinline__ void draw2_3(const uint4 e, const uint4 f, uint32_t B1, uint32_t h0c,
                                         uint32_t l0c, const KParams& p, uint32_t (&W)[4],
                                         uint32_t (&V)[4]) {
-    uint32_t x0 = e.c0k ^ B1, x1 = e.c1, x2 = h0c ^ e.c2k, x3 = l0c;
-    uint32_t y0 = f.c0k ^ B1, y1 = f.c1, y2 = h0c ^ f.c2k, y3 = l0c;
+    uint32_t x0 = e.x ^ B1, x1 = e.y, x2 = h0c ^ e.z, x3 = l0c;
+    uint32_t y0 = f.x ^ B1, y1 = f.y, y2 = h0c ^ f.z, y3 = l0c;
 #pragma unroll
     for (int rr = 3; rr < 10; ++rr) {
         uint32_t hi0, lo0, hi1, lo1, gi0, go0, gi1, go1;
@@ -100,9 +101,9 @@ __device__ __forceinline__ void draw2_3(const Tab3& e, const Tab3& f, uint32_t B
     V[0] = y0; V[1] = y1; V[2] = y2; V[3] = y3;
 }
 
-__device__ __forceinline__ void draw1_3(const Tab3& e, uint32_t B1, uint32_t h0c, uint32_t l0c,
+__device__ __forceinline__ void draw1_3(const uint4 e, uint32_t B1, uint32_t h0c, uint32_t l0c,
                                         const KParams& p, uint32_t (&W)[4]) {
-    uint32_t x0 = e.c0k ^ B1, x1 = e.c1, x2 = h0c ^ e.c2k, x3 = l0c;
+    uint32_t x0 = e.x ^ B1, x1 = e.y, x2 = h0c ^ e.z, x3 = l0c;
 #pragma unroll
     for (int rr = 3; rr < 10; ++rr) {
         uint32_t hi0, lo0, hi1, lo1;
@@ -131,52 +132,90 @@ __device__ __forceinline__ void classes3(uint32_t P0, uint32_t P1, uint32_t P2, 
     c4 = ~n2 & n1 & ~n0;
 }
 
-__device__ __forceinline__ void cmp8_3(uint32_t c4, uint32_t c8, uint32_t c12, const Tab3& e,
-                                       const Tab3& f, const uint32_t (&W)[4],
-                                       const uint32_t (&V)[4], uint32_t& b, uint32_t& eq) {
+// threshold bits of a plane block for the three classes (0 or 1 per plane)
+struct BlockBits {
+    uint4 b4, b8, b12;
+};
+
+__device__ __forceinline__ uint32_t lane4(const uint4 v, int m) {
+    return m == 0 ? v.x : (m == 1 ? v.y : (m == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ uint32_t thr_word(uint32_t c4, uint32_t c8, uint32_t c12,
+                                             const BlockBits& t, int m) {
+    return c4 * lane4(t.b4, m) + c8 * lane4(t.b8, m) + c12 * lane4(t.b12, m);
+}
+
+// planes 0-7 by the borrow of the subtraction from the least significant plane up
+__device__ __forceinline__ void cmp8_3(uint32_t c4, uint32_t c8, uint32_t c12, const BlockBits* bt,
+                                       const uint32_t (&W)[4], const uint32_t (&V)[4],
+                                       uint32_t& b, uint32_t& eq) {
     b = 0u;
     eq = 0xFFFFFFFFu;
+    const BlockBits f = bt[1];
 #pragma unroll
     for (int m = 3; m >= 0; --m) {
-        const uint32_t t = c4 * f.B0[m] + c8 * f.B1[m] + c12 * f.B2[m];
+        const uint32_t t = thr_word(c4, c8, c12, f, m);
         b = (~V[m] & t) | (~(V[m] ^ t) & b);
         eq &= ~(V[m] ^ t);
     }
+    const BlockBits e = bt[0];
 #pragma unroll
     for (int m = 3; m >= 0; --m) {
-        const uint32_t t = c4 * e.B0[m] + c8 * e.B1[m] + c12 * e.B2[m];
+        const uint32_t t = thr_word(c4, c8, c12, e, m);
         b = (~W[m] & t) | (~(W[m] ^ t) & b);
         eq &= ~(W[m] ^ t);
     }
 }
 
-__device__ __forceinline__ void finish3(uint32_t c4, uint32_t c8, uint32_t c12, const Tab3* tab,
-                                        uint32_t B1, uint32_t h0c, uint32_t l0c,
-                                        const KParams& p, uint32_t& und, uint32_t& lt) {
+// plane blocks 2-7 of an undecided site, block by block from the top
+__device__ __forceinline__ void finish3(uint32_t c4, uint32_t c8, uint32_t c12, const uint2* bpart,
+                                        const BlockBits* bt, uint32_t l0a, uint32_t B1,
+                                        uint32_t h0c, uint32_t l0c, const KParams& p,
+                                        uint32_t& und, uint32_t& lt) {
 #pragma unroll 1
     for (int g = 2; g < 8 && und; ++g) {
         uint32_t W[4];
-        draw1_3(tab[g], B1, h0c, l0c, p, W);
+        draw1_3(group_part(p, bpart[g], l0a), B1, h0c, l0c, p, W);
+        const BlockBits t = bt[g];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const uint32_t t = c4 * tab[g].B0[m] + c8 * tab[g].B1[m] + c12 * tab[g].B2[m];
-            lt |= und & t & ~W[m];
-            und &= ~(W[m] ^ t);
+            const uint32_t tm = thr_word(c4, c8, c12, t, m);
+            lt |= und & tm & ~W[m];
+            und &= ~(W[m] ^ tm);
         }
     }
 }
 
-// site-table entry: x = lattice word (group offset included) | group << 16,
-//                   y = Philox site index | faces << 16 (bit f: the site is on the
-//                   face x = 0, x = L-1, y = 0, y = L-1, z = 0, z = L-1)
-template <int L>
-__device__ __forceinline__ uint2 site_entry(int g, int s) {
-    using S = Shape3<L>;
-    const int x = s % L, y = (s / L) % L, z = s / (L * L);
-    const uint32_t faces = (x == 0 ? 1u : 0u) | (x == L - 1 ? 2u : 0u) | (y == 0 ? 4u : 0u) |
-                           (y == L - 1 ? 8u : 0u) | (z == 0 ? 16u : 0u) | (z == L - 1 ? 32u : 0u);
-    return make_uint2((uint32_t)(g * S::CELLS + S::cell(x, y, z)) | ((uint32_t)g << 16),
-                      (uint32_t)s | (faces << 16));
+// all-ones if the sign bit of byte SEL & 3 of v is set, else zero (prmt with
+// every selector nibble 8 + byte replicates the selected byte's sign bit)
+template <int SEL>
+__device__ __forceinline__ uint32_t sign_of_byte(uint32_t v) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %1, %2;" : "=r"(r) : "r"(v), "n"(SEL));
+    return r;
+}
+
+// the six bond planes of a site: j holds its bond signs as byte sign bits, x
+// bytes 0-3 the bonds to +x, -x, +y, -y and y bytes 0-1 those to +z, -z
+template <int L, bool EA>
+__device__ __forceinline__ void bond_planes(const uint32_t* la, uint2 j, uint32_t w,
+                                            uint32_t (&P)[6]) {
+    constexpr int PP = L + 2, P2 = PP * PP;
+    P[0] = w ^ la[1];
+    P[1] = w ^ la[-1];
+    P[2] = w ^ la[PP];
+    P[3] = w ^ la[-PP];
+    P[4] = w ^ la[P2];
+    P[5] = w ^ la[-P2];
+    if (EA) {
+        P[0] ^= sign_of_byte<0x8888>(j.x);
+        P[1] ^= sign_of_byte<0x9999>(j.x);
+        P[2] ^= sign_of_byte<0xAAAA>(j.x);
+        P[3] ^= sign_of_byte<0xBBBB>(j.x);
+        P[4] ^= sign_of_byte<0x8888>(j.y);
+        P[5] ^= sign_of_byte<0x9999>(j.y);
+    }
 }
 
 // store a flipped site and its halo copies
@@ -192,39 +231,47 @@ __device__ __forceinline__ void store_site(uint32_t* la, uint32_t v, uint32_t fa
     if (faces & 32u) la[-L * P2] = v;
 }
 
-template <int L, bool EA>
-__device__ __forceinline__ void bond_planes(const uint32_t* la, const uint4* jw, uint32_t s,
-                                            uint32_t w, uint32_t (&P)[6]) {
-    constexpr int PP = L + 2, P2 = PP * PP;
-    P[0] = w ^ la[1];
-    P[1] = w ^ la[-1];
-    P[2] = w ^ la[PP];
-    P[3] = w ^ la[-PP];
-    P[4] = w ^ la[P2];
-    P[5] = w ^ la[-P2];
-    if (EA) {
-        const uint4 a = jw[2 * s], b = jw[2 * s + 1];
-        P[0] ^= a.x;
-        P[1] ^= a.y;
-        P[2] ^= a.z;
-        P[3] ^= a.w;
-        P[4] ^= b.x;
-        P[5] ^= b.y;
-    }
+// site-table entry of site s: x = lattice word in group 0 | faces << 16 (bit f:
+// the site is on the face x = 0, x = L-1, y = 0, y = L-1, z = 0, z = L-1),
+// y = s
+template <int L>
+__device__ __forceinline__ uint2 site_entry(int s) {
+    using S = Shape3<L>;
+    const int x = s % L, y = (s / L) % L, z = s / (L * L);
+    const uint32_t faces = (x == 0 ? 1u : 0u) | (x == L - 1 ? 2u : 0u) | (y == 0 ? 4u : 0u) |
+                           (y == L - 1 ? 8u : 0u) | (z == 0 ? 16u : 0u) | (z == L - 1 ? 32u : 0u);
+    return make_uint2((uint32_t)S::cell(x, y, z) | (faces << 16), (uint32_t)s);
+}
+
+// the bond-sign word of site s (layout of bond_planes) from the coupling bits
+// (bit a of jbits[s]: bond (s, s + e_a) has J = -1)
+template <int L>
+__device__ __forceinline__ uint2 bond_entry(const uint8_t* jbits, int s) {
+    const int x = s % L, y = (s / L) % L, z = s / (L * L);
+    const uint32_t js = jbits[s];
+    const uint32_t jxm = jbits[z * L * L + y * L + (x + L - 1) % L];
+    const uint32_t jym = jbits[z * L * L + ((y + L - 1) % L) * L + x];
+    const uint32_t jzm = jbits[((z + L - 1) % L) * L * L + y * L + x];
+    const uint32_t bx = ((js & 1u) << 7) | ((jxm & 1u) << 15) | (((js >> 1) & 1u) << 23) |
+                        (((jym >> 1) & 1u) << 31);
+    const uint32_t by = (((js >> 2) & 1u) << 7) | (((jzm >> 2) & 1u) << 15);
+    return make_uint2(bx, by);
 }
 
 template <int L, bool EA>
-__global__ void __launch_bounds__(NT3, 8) k_sweep3d(KParams p, const uint32_t* cta2run) {
+__global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* cta2run) {
     using S = Shape3<L>;
     constexpr int G = S::G, H = S::H, N = S::N, P = S::P, P2 = S::P2, NW = NT3 / 32;
     constexpr int W = S::W, WP = S::WP;
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t* lat = smem;                                               // G halo lattices
-    uint2* stab = reinterpret_cast<uint2*>(smem + S::LAT_WORDS);       // 2 x TAB entries
-    uint4* jw = reinterpret_cast<uint4*>(stab + 2 * S::TAB);           // EA: 2 uint4 per site
-    uint4* qbase = jw + (EA ? 2 * N : 0);                              // NW x (QW + 32)
-    __shared__ __align__(16) Tab3 tabs[2][G][8];
-    __shared__ uint32_t sA2x[G], sVm[G];
+    uint2* stab = reinterpret_cast<uint2*>(smem + S::LAT_WORDS);       // 2 x H site entries
+    uint2* jq = stab + 2 * H;                                          // EA: 2 x H bond words
+    uint4* qbase = reinterpret_cast<uint4*>(jq + (EA ? 2 * H : 0));    // NW x (QW + 32)
+    __shared__ __align__(16) uint4 gtab[2][G][2];  // group parts of blocks 0, 1 per half-sweep
+    __shared__ uint2 bpart[2][8];                  // block parts per half-sweep
+    __shared__ BlockBits btab[8];                  // threshold bits of the step's classes
+    __shared__ uint32_t sA2x[G], sL0a[G], sVm[G];
     __shared__ int32_t sU[G][32], sNup[G][32];
     __shared__ unsigned long long sAcc;
 
@@ -241,10 +288,10 @@ __global__ void __launch_bounds__(NT3, 8) k_sweep3d(KParams p, const uint32_t* c
     const int qcap = (p.qcap_limit >= 0 && p.qcap_limit < S::QW) ? p.qcap_limit : S::QW;
     const int qflush = qcap >= 32 ? qcap - 32 : 0;
 
-    // per-group Philox part and valid-replica masks
-    uint32_t B1k;
+    // Philox parts of the step, the groups' counters and the valid-replica masks
+    uint32_t B1k, h1a;
     {
-        uint32_t h1a, l1a;
+        uint32_t l1a;
         mulhilo(PHILOX_M1, (uint32_t)i, h1a, l1a);
         B1k = l1a ^ p.rk0[1];
     }
@@ -256,6 +303,17 @@ __global__ void __launch_bounds__(NT3, 8) k_sweep3d(KParams p, const uint32_t* c
         uint32_t h0a, l0a;
         mulhilo(PHILOX_M0, r.grp0 + gfirst + g, h0a, l0a);
         sA2x[g] = h0a ^ p.rk1[0];
+        sL0a[g] = l0a;
+    }
+    const uint32_t* thr = r.sthr + 4 * (i - 1);
+    if (threadIdx.x < 8 * 3) {
+        const int b = threadIdx.x / 3, k = threadIdx.x % 3;
+        const uint32_t tk = thr[k + 1];
+        const uint4 v = make_uint4((tk >> (31 - 4 * b)) & 1u, (tk >> (30 - 4 * b)) & 1u,
+                                   (tk >> (29 - 4 * b)) & 1u, (tk >> (28 - 4 * b)) & 1u);
+        if (k == 0) btab[b].b4 = v;
+        else if (k == 1) btab[b].b8 = v;
+        else btab[b].b12 = v;
     }
     for (int k = threadIdx.x; k < G * 32; k += NT3) {
         sU[k >> 5][k & 31] = 0;
@@ -285,26 +343,15 @@ __global__ void __launch_bounds__(NT3, 8) k_sweep3d(KParams p, const uint32_t* c
             }
         }
     }
-    // site tables of the two colours, and the bond signs (EA)
-    for (int k = threadIdx.x; k < 2 * S::TAB; k += NT3) {
-        const int colour = k / S::TAB, e = k % S::TAB;
-        const int g = e / H, q = e % H;
+    // site tables of the two colours (site q of a colour: s = 2q or 2q + 1), and
+    // the bond signs (EA)
+    for (int k = threadIdx.x; k < 2 * H; k += NT3) {
+        const int colour = k / H, q = k % H;
         const int s0 = 2 * q;
         const int x0 = s0 % L, yz = s0 / L;
         const int s = s0 + ((((yz % L) + (yz / L) + x0) & 1) != colour ? 1 : 0);
-        stab[k] = site_entry<L>(g, s);
-    }
-    if (EA) {
-        for (int s = threadIdx.x; s < N; s += NT3) {
-            const int x = s % L, y = (s / L) % L, z = s / (L * L);
-            const uint32_t js = r.jbits[s];
-            const uint32_t jxm = r.jbits[z * L * L + y * L + (x + L - 1) % L];
-            const uint32_t jym = r.jbits[z * L * L + ((y + L - 1) % L) * L + x];
-            const uint32_t jzm = r.jbits[((z + L - 1) % L) * L * L + y * L + x];
-            jw[2 * s] = make_uint4(0u - (js & 1u), 0u - (jxm & 1u), 0u - ((js >> 1) & 1u),
-                                   0u - ((jym >> 1) & 1u));
-            jw[2 * s + 1] = make_uint4(0u - ((js >> 2) & 1u), 0u - ((jzm >> 2) & 1u), 0u, 0u);
-        }
+        stab[k] = site_entry<L>(s);
+        if (EA) jq[k] = bond_entry<L>(r.jbits, s);
     }
     __syncthreads();
     // periodic copies in the halo faces
@@ -322,39 +369,49 @@ __global__ void __launch_bounds__(NT3, 8) k_sweep3d(KParams p, const uint32_t* c
         }
         lg[d] = lg[sidx];
     }
-
+    // Philox tables of half-sweep hh: the block parts (all eight blocks) and the
+    // groups' parts of blocks 0 and 1
+    auto build_tables = [&](uint32_t hh) {
+        const uint32_t t = hh >> 1;
+        const int colour = (int)(hh & 1u);
+        for (int k = threadIdx.x; k < 8 + 2 * G; k += NT3) {
+            if (k < 8) {
+                bpart[hh & 1u][k] = block_part(p, h1a, t, colour, k);
+            } else {
+                const int g = (k - 8) >> 1, b = (k - 8) & 1;
+                gtab[hh & 1u][g][b] = group_part(p, block_part(p, h1a, t, colour, b), sL0a[g]);
+            }
+        }
+    };
     const uint32_t nh = 2u * r.stheta[i - 1];
-    const uint32_t* thr = r.sthr + 4 * (i - 1);
-    if (nh > 0 && threadIdx.x < 8 * G)
-        build_tab3(tabs[0][threadIdx.x >> 3], threadIdx.x & 7, p, r.grp0 + gfirst + (threadIdx.x >> 3),
-                   (uint32_t)i, 0u, 0, thr);
+    if (nh > 0) build_tables(0u);
     __syncthreads();
 
     const uint32_t lml = (1u << lane) - 1u;
     uint32_t acc = 0;
     for (uint32_t h = 0; h < nh; ++h) {
         const int colour = (int)(h & 1u);
-        if (h + 1 < nh && threadIdx.x < 8 * G)
-            build_tab3(tabs[(h + 1) & 1u][threadIdx.x >> 3], threadIdx.x & 7, p,
-                       r.grp0 + gfirst + (threadIdx.x >> 3), (uint32_t)i, (h + 1) >> 1,
-                       (int)((h + 1) & 1u), thr);
-        const uint2* ct = stab + colour * S::TAB;
+        if (h + 1 < nh) build_tables(h + 1);
+        const uint2* ct = stab + colour * H;
+        const uint2* cj = jq + colour * H;
+        const uint4(*gt)[2] = gtab[h & 1u];
         int k = 0;
         while (true) {
             int wq = 0;
 #pragma unroll 1
             for (; k < S::ITERS && wq <= qflush; ++k) {
                 const int e = threadIdx.x + k * NT3;
-                const bool have = e < S::TAB;
-                // lanes past the table run entry 0 with no valid replica (no flip, no queue)
-                const uint2 en = ct[have ? e : 0];
-                const int g = (int)(en.x >> 16);
-                uint32_t* la = lat + (en.x & 0xFFFFu);
-                const uint32_t s = en.y & 0xFFFFu;
+                const bool have = e < G * H;
+                // lanes past the work items run item 0 with no valid replica
+                const int ee = have ? e : 0;
+                const int g = ee / H, q = ee - g * H;
+                const uint2 en = ct[q];
+                uint32_t* la = lat + g * S::CELLS + (en.x & 0xFFFFu);
+                const uint32_t s = en.y;
                 const uint32_t vm = have ? sVm[g] : 0u;
                 const uint32_t w = la[0];
                 uint32_t Pb[6];
-                bond_planes<L, EA>(la, jw, s, w, Pb);
+                bond_planes<L, EA>(la, EA ? cj[q] : make_uint2(0u, 0u), w, Pb);
                 uint32_t need, c4, c8, c12;
                 classes3(Pb[0], Pb[1], Pb[2], Pb[3], Pb[4], Pb[5], vm, need, c4, c8, c12);
                 const uint32_t A2s = sA2x[g] ^ s;
@@ -365,47 +422,45 @@ __global__ void __launch_bounds__(NT3, 8) k_sweep3d(KParams p, const uint32_t* c
                     B1 = l1b;
                     mulhilo(PHILOX_M0, h1b ^ B1k, h0c, l0c);
                 }
-                const Tab3* tb = tabs[h & 1u][g];
                 uint32_t Wd[4], Vd[4];
-                draw2_3(tb[0], tb[1], B1, h0c, l0c, p, Wd, Vd);
+                draw2_3(gt[g][0], gt[g][1], B1, h0c, l0c, p, Wd, Vd);
                 uint32_t b, eq;
-                cmp8_3(c4, c8, c12, tb[0], tb[1], Wd, Vd, b, eq);
+                cmp8_3(c4, c8, c12, btab, Wd, Vd, b, eq);
                 const uint32_t lt = b & need;
                 const uint32_t und = eq & need;
                 const bool undecided = und != 0u;
                 const uint32_t ball = __ballot_sync(0xFFFFFFFFu, undecided);
                 const int slot = undecided ? wq + __popc(ball & lml) : S::QW + lane;
-                queue[slot] = make_uint4(A2s, und, lt, (uint32_t)e);
+                queue[slot] = make_uint4(A2s, und, lt, (uint32_t)ee);
                 const uint32_t f = (~need | lt) & (undecided ? 0u : vm);
-                if (have) store_site<L>(la, w ^ f, en.y >> 16);
+                if (have) store_site<L>(la, w ^ f, en.x >> 16);
                 acc += (uint32_t)__popc(f);
                 wq += __popc(ball);
             }
             // the warp's undecided sites, one per lane, from plane block 2 on
             __syncwarp();
             for (int e2 = lane; e2 < wq; e2 += 32) {
-                const uint4 q = queue[e2];
-                const uint2 en = ct[q.w];
-                const int g = (int)(en.x >> 16);
-                uint32_t* la = lat + (en.x & 0xFFFFu);
-                const uint32_t s = en.y & 0xFFFFu;
+                const uint4 qe = queue[e2];
+                const int g = (int)qe.w / H, q = (int)qe.w - g * H;
+                const uint2 en = ct[q];
+                uint32_t* la = lat + g * S::CELLS + (en.x & 0xFFFFu);
                 const uint32_t vm = sVm[g];
                 const uint32_t w = la[0];
                 uint32_t Pb[6];
-                bond_planes<L, EA>(la, jw, s, w, Pb);
+                bond_planes<L, EA>(la, EA ? cj[q] : make_uint2(0u, 0u), w, Pb);
                 uint32_t need, c4, c8, c12;
                 classes3(Pb[0], Pb[1], Pb[2], Pb[3], Pb[4], Pb[5], vm, need, c4, c8, c12);
                 uint32_t B1, h0c, l0c;
                 {
                     uint32_t h1b, l1b;
-                    mulhilo(PHILOX_M1, q.x, h1b, l1b);
+                    mulhilo(PHILOX_M1, qe.x, h1b, l1b);
                     B1 = l1b;
                     mulhilo(PHILOX_M0, h1b ^ B1k, h0c, l0c);
                 }
-                uint32_t und = q.y, lt = q.z;
-                finish3(c4, c8, c12, tabs[h & 1u][g], B1, h0c, l0c, p, und, lt);
+                uint32_t und = qe.y, lt = qe.z;
+                finish3(c4, c8, c12, bpart[h & 1u], btab, sL0a[g], B1, h0c, l0c, p, und, lt);
                 const uint32_t f = (~need | lt) & vm;
-                store_site<L>(la, w ^ f, en.y >> 16);
+                store_site<L>(la, w ^ f, en.x >> 16);
                 acc += (uint32_t)__popc(f);
             }
             __syncwarp();
@@ -435,10 +490,10 @@ __global__ void __launch_bounds__(NT3, 8) k_sweep3d(KParams p, const uint32_t* c
                     P1 = w ^ lg[c + P];
                     P2v = w ^ lg[c + P2];
                     if (EA) {
-                        const uint4 a = jw[2 * s], bb = jw[2 * s + 1];
-                        P0 ^= a.x;
-                        P1 ^= a.z;
-                        P2v ^= bb.x;
+                        const uint32_t js = r.jbits[s];
+                        P0 ^= 0u - (js & 1u);
+                        P1 ^= 0u - ((js >> 1) & 1u);
+                        P2v ^= 0u - ((js >> 2) & 1u);
                     }
                 }
                 const uint32_t tw = transpose32(w, lane);
@@ -494,7 +549,7 @@ __global__ void __launch_bounds__(NT3, 8) k_sweep3d(KParams p, const uint32_t* c
 template <int L, bool EA>
 size_t smem3d() {
     using S = Shape3<L>;
-    return (size_t)S::LAT_WORDS * 4 + (size_t)2 * S::TAB * 8 + (EA ? (size_t)S::N * 32 : 0) +
+    return (size_t)S::LAT_WORDS * 4 + (size_t)2 * S::H * 8 * (EA ? 2 : 1) +
            (size_t)(NT3 / 32) * (S::QW + 32) * 16;
 }
 

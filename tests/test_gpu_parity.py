@@ -112,7 +112,9 @@ def test_3d_spin_glass_ragged(method):
 @pytest.mark.parametrize("d,L,R,kind", [(2, 6, 70, "ferro"), (2, 10, 100, "ea"),
                                         (3, 4, 257, "ea"), (3, 10, 64, "ferro"),
                                         (2, 2, 40, "ferro"), (3, 2, 33, "ea"),
-                                        (2, 32, 96, "ferro"), (2, 4, 1, "ferro")])
+                                        (2, 32, 96, "ferro"), (2, 4, 1, "ferro"),
+                                        (3, 8, 300, "ea"), (3, 12, 45, "ferro"),
+                                        (3, 14, 40, "ea"), (3, 16, 70, "ea")])
 def test_lattice_shapes(d, L, R, kind):
     # a single replica under Poisson resampling dies out with probability 1/e per step
     for method in (("systematic", "poisson") if R > 8 else ("systematic", "nearest")):
