@@ -25,13 +25,15 @@
 
 namespace pa {
 
-__device__ __forceinline__ double pow_bin(double q, uint32_t k) {
-    double r = 1.0, b = q;
-    while (k) {
-        if (k & 1u) r = __dmul_rn(r, b);
-        b = __dmul_rn(b, b);
-        k >>= 1;
-    }
+// q^k by binary powering from a table of the squares qsq[m] = q^(2^m), each the
+// rounded square of the one before (qsq[0] = q): the product of the squares of
+// the set bits of k, least significant first, every multiply rounded -- the
+// same value as squaring and multiplying in one loop, with popc(k) multiplies
+// on the dependent chain.
+__device__ __forceinline__ double pow_tab(const double* qsq, uint32_t k) {
+    double r = 1.0;
+    for (int m = 0; k; ++m, k >>= 1)
+        if (k & 1u) r = __dmul_rn(r, qsq[m]);
     return r;
 }
 
@@ -165,45 +167,77 @@ __device__ double max_threads(double v, double* sh) {
 
 // --------------------------------------------------------------------------
 // K3: weights, S, ln Q, f table (one CTA)
+//
+// One CTA of 1024 threads; its time is latency, not work, so the phases are
+// kept few: the level counts are read from global memory once (into shared
+// memory, while the occupied range is found), the logarithms of ln Q run on a
+// warp that has no level of its own while the others compute f.
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_weights(KParams p) {
     const RunDesc& r = p.runs[blockIdx.x];
     DevState* st = r.st;
     if (st->status != S_OK) return;
+    constexpr int TREE_SMEM = 2048;
+    // tree and weights; before the tree is built, the level counts (cached when
+    // the nlev 32-bit counts fit in its 4 TREE_SMEM words)
+    __shared__ double tw[2 * TREE_SMEM];
+    double* tsm = tw;
+    double* wsm = tw + TREE_SMEM;
+    uint32_t* hc = reinterpret_cast<uint32_t*>(tw);
     __shared__ int smin[32], smax[32];
+    __shared__ double qsq[32], S_sh, lnS_sh, lnR_sh;
     const int i = st->step + 1;
     const uint32_t Rprev = st->R_cur;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (int)(blockDim.x >> 5);
+    const bool cached = r.nlev <= 4 * TREE_SMEM;
     int lo = INT_MAX, hi = -1;
-    for (int l = threadIdx.x; l < r.nlev; l += blockDim.x)
-        if (r.hist[l]) {
+#pragma unroll 4
+    for (int l = threadIdx.x; l < r.nlev; l += blockDim.x) {
+        const uint32_t c = r.hist[l];
+        if (cached) hc[l] = c;
+        if (c) {
             lo = min(lo, l);
             hi = max(hi, l);
         }
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
     if (lane == 0) {
         smin[warp] = lo;
         smax[warp] = hi;
     }
     __syncthreads();
-    lo = INT_MAX;
-    hi = -1;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        lo = min(lo, smin[w]);
-        hi = max(hi, smax[w]);
-    }
+    lo = __reduce_min_sync(0xffffffffu, lane < nwarps ? smin[lane] : INT_MAX);
+    hi = __reduce_max_sync(0xffffffffu, lane < nwarps ? smax[lane] : -1);
     const int lmin = lo;
     const int K = hi - lo + 1;
     int P = 1;
     while (P < K) P <<= 1;
     const double q = r.sq[i - 1];
+    // the squares q^(2^m) for the bits of k < K
+    if (threadIdx.x == 0) {
+        const int nb = K > 1 ? 32 - __clz(K - 1) : 0;
+        double b = q;
+        for (int m = 0; m < nb; ++m) {
+            qsq[m] = b;
+            b = __dmul_rn(b, b);
+        }
+    }
+    const bool in_smem = P <= TREE_SMEM;
+    // the counts of the thread's levels k = threadIdx.x + j blockDim.x, j < 2 (all
+    // of them when the tree is in shared memory)
+    uint32_t n0 = 0u, n1 = 0u;
+    if (in_smem) {
+        const int k0 = threadIdx.x, k1 = threadIdx.x + blockDim.x;
+        if (k0 < K) n0 = cached ? hc[lmin + k0] : r.hist[lmin + k0];
+        if (k1 < K) n1 = cached ? hc[lmin + k1] : r.hist[lmin + k1];
+    }
+    __syncthreads();  // qsq written; the count cache is free for the tree
     if (p.alpha >= 0.0) {
         // partial resampling: the level factors q^k; k_pw_final closes the step
         double* wl = reinterpret_cast<double*>(r.flev);
-        for (int k = threadIdx.x; k < K; k += blockDim.x) wl[k] = pow_bin(q, (uint32_t)k);
+        for (int k = threadIdx.x; k < K; k += blockDim.x) wl[k] = pow_tab(qsq, (uint32_t)k);
         __syncthreads();
         for (int k = threadIdx.x; k < K; k += blockDim.x) r.hist[lmin + k] = 0u;
         if (threadIdx.x == 0) {
@@ -223,47 +257,65 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
     // the zero-padded array: in shared memory when it fits (the usual case: the
     // occupied levels span a few hundred), else in the run's global scratch; the
     // last five levels by warp shuffles with the same pairs
-    constexpr int TREE_SMEM = 2048;
-    __shared__ double tsm[TREE_SMEM], wsm[TREE_SMEM];
-    const bool in_smem = P <= TREE_SMEM;
-    volatile double* t = in_smem ? tsm : r.tree;
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
-        double v = 0.0;
-        if (k < K) {
-            const double wk = pow_bin(q, (uint32_t)k);
-            if (in_smem) wsm[k] = wk;
-            v = __dmul_rn((double)r.hist[lmin + k], wk);
-        }
-        t[k] = v;
-    }
-    __threadfence_block();
-    __syncthreads();
     int h = P >> 1;
-    for (; h >= 32; h >>= 1) {
-        for (int k = threadIdx.x; k < h; k += blockDim.x) t[k] = __dadd_rn(t[k], t[k + h]);
+    if (in_smem) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int k = threadIdx.x + j * blockDim.x;
+            if (k < P) {
+                double v = 0.0;
+                if (k < K) {
+                    const double wk = pow_tab(qsq, (uint32_t)k);
+                    wsm[k] = wk;
+                    v = __dmul_rn((double)(j == 0 ? n0 : n1), wk);
+                }
+                tsm[k] = v;
+            }
+        }
+        __syncthreads();
+        for (; h >= 32; h >>= 1) {
+            for (int k = threadIdx.x; k < h; k += blockDim.x)
+                tsm[k] = __dadd_rn(tsm[k], tsm[k + h]);
+            __syncthreads();
+        }
+    } else {
+        volatile double* t = r.tree;
+        for (int k = threadIdx.x; k < P; k += blockDim.x)
+            t[k] = k < K ? __dmul_rn((double)r.hist[lmin + k], pow_tab(qsq, (uint32_t)k)) : 0.0;
         __threadfence_block();
         __syncthreads();
+        for (; h >= 32; h >>= 1) {
+            for (int k = threadIdx.x; k < h; k += blockDim.x) t[k] = __dadd_rn(t[k], t[k + h]);
+            __threadfence_block();
+            __syncthreads();
+        }
     }
-    __shared__ double S_sh;
     if (warp == 0) {
         const int live = h > 0 ? 2 * h : 1;  // entries left after the shared-memory levels
+        const volatile double* t = in_smem ? tsm : r.tree;
         double v = lane < live ? t[lane] : 0.0;
         for (; h >= 1; h >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, h));
         if (lane == 0) S_sh = v;
     }
     __syncthreads();
     const double S = S_sh;
+    // ln S and ln R_{i-1} on the last warp (lanes 0 and 1, one pass), before its levels
+    if (warp == nwarps - 1) {
+        const double lx = log(lane == 0 ? S : (double)Rprev);
+        if (lane == 0) lnS_sh = lx;
+        if (lane == 1) lnR_sh = lx;
+    }
     const double Rd = (double)r.R;
     // f_k, and the totals T = sum_j f_j = sum_k n_k f_k and of the fractional parts
     // (exact integer sums; the copy-count kernels need them before any scan)
     unsigned long long sT = 0, sTr = 0;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        double a = __dmul_rn(Rd, in_smem ? wsm[k] : pow_bin(q, (uint32_t)k));
+    for (int k = threadIdx.x, j = 0; k < K; k += blockDim.x, ++j) {
+        double a = __dmul_rn(Rd, in_smem ? wsm[k] : pow_tab(qsq, (uint32_t)k));
         a = __ddiv_rn(a, S);
         a = scalbn(a, FRAC_BITS);
         const uint64_t f = (uint64_t)floor(a);
         r.flev[k] = f;
-        const uint64_t n = r.hist[lmin + k];
+        const uint64_t n = in_smem ? (j == 0 ? n0 : n1) : r.hist[lmin + k];
         sT += n * f;
         sTr += n * (f & ((1ull << FRAC_BITS) - 1));
     }
@@ -288,7 +340,7 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
         st->kmax = 0;
         const int32_t Umin = 2 * lmin + r.parity;
         const int32_t Emin = 2 * Umin - p.d * r.N;
-        const double lnQ = __dsub_rn(__dsub_rn(log(S), log((double)Rprev)),
+        const double lnQ = __dsub_rn(__dsub_rn(lnS_sh, lnR_sh),
                                      __dmul_rn(r.sdbeta[i - 1], (double)Emin));
         st->R_prev = Rprev;
         st->lmin = (uint32_t)lmin;
