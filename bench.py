@@ -1001,6 +1001,41 @@ def run_partial(args):
     return 0
 
 
+def run_split(args):
+    """Where a temperature step's time goes: 2D Ising L=64, beta 0 -> 1 in 200 steps, for
+    R = 3000 / 30000 / 100000 (theta = 10 / 5 / 10) and three copy-count rules; the whole
+    run replayed as graphs (device time of all 200 steps, CUDA events) against the sweep
+    kernel alone (its launches timed by the library's own events in a second run of the
+    same seed).  outside_sweep = 1 - sweep time / step time."""
+    import torch
+    from paper_2401_07965_gb300 import pa
+    n = 200
+    betas = np.linspace(0.0, 1.0, n + 1)
+    stream = torch.cuda.Stream()
+    out = {}
+    for rule in ("systematic", "nearest", "multinomial"):
+        for R, th in ((3000, 10), (30000, 5), (100000, 10)):
+            thetas = np.full(n, th, np.uint32)
+            b = pa.Batch([{"dim": 2, "L": 64, "R": R}], betas, thetas, rule, 11, stream=stream)
+            ms = _timed_batch(pa, b, n, stream)
+            b.close()
+            p = pa.Population(2, 64, R, betas, thetas, rule, 11, stream=stream)
+            pa.pa_enable_timing(p.ctx, True)
+            p.step(n)
+            sms, cnt, _ = pa.pa_sweep_timing(p.ctx)
+            p.close()
+            out[f"{rule} R={R} theta={th}"] = {
+                "us_per_step": 1e3 * ms / n, "sweep_us_per_step": 1e3 * sms / cnt,
+                "outside_sweep": 1.0 - (sms / cnt) / (ms / n)}
+    key = "systematic R=30000 theta=5"
+    _line("step split: 2D Ising L=64, beta 0->1 in 200 steps; R = 3000 / 30000 / 100000, "
+          "systematic / nearest / multinomial", out[key]["outside_sweep"],
+          out[key]["us_per_step"] * n / 1e3, n, 0,
+          {"unit": "fraction of step time outside the sweep kernel",
+           "higher_is_better": False, "what": key, "split": out})
+    return 0
+
+
 def run_e2e(args, pa, stream, seed, dev, threads=0):
     """Whole runs through the C ABI: host schedule -> pa_init -> per step pa_step +
     pa_observables (device -> host) -> pa_free_energy.  Host wall clock."""
@@ -1061,12 +1096,13 @@ def main():
                     help="small: one run of R=20000 replicas of the same lattice (profiling)")
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "ea3d", "weighted", "accuracy", "controller",
-                             "overlap", "partial"],
+                             "overlap", "partial", "split"],
                     help="headline: the benchmark line; ea3d / weighted: the batched "
                          "workloads; accuracy: time to a free energy within 1e-4 per spin; "
                          "controller: learned against plain schedule; overlap: P(q) of "
                          "two populations per spin-glass sample; partial: resampling only "
-                         "when the weights' effective size is low")
+                         "when the weights' effective size is low; split: step time "
+                         "outside the sweep kernel")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1086,6 +1122,8 @@ def main():
         return run_overlap(args)
     if args.workload == "partial":
         return run_partial(args)
+    if args.workload == "split":
+        return run_split(args)
     return run_ours(args)
 
 
