@@ -250,6 +250,16 @@ int32_t pa_get_sweep_threads(const pa_ctx *ctx);
  * PA_ERR_ARG for cap < -1. */
 pa_status pa_set_sweep_queue(pa_ctx *ctx, int32_t cap);
 
+/* Test hook of the failure path (no counterpart in the paper).  The scans of the
+ * copy numbers (Sec. 2 step 2) are single-pass: a block waits, by a bounded
+ * spin, for the prefix its predecessor publishes.  With on = 1 the first block
+ * of every run withholds its prefix, so the other blocks' waits run out after
+ * their bound (about a second) and the step ends with PA_ERR_TIMEOUT: nothing
+ * faults or hangs, and the context then accepts queries and pa_destroy only.
+ * on = 0 (the default) restores normal operation before a failure.  PA_ERR_ARG
+ * for a null context or another value of on. */
+pa_status pa_set_wait_test(pa_ctx *ctx, int32_t on);
+
 /* Reweighting of one temperature step without any device allocation.
  *
  * Some callers cannot call cudaMalloc: code embedded in a host framework that

@@ -578,6 +578,7 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     p.ctl = nullptr;
     p.alpha = -1.0;
     p.qcap_limit = -1;
+    p.lb_hold = 0;
     p.L_all = ctx->runs[0].L;
     for (const RunHost& h : ctx->runs)
         if (h.L != p.L_all) p.L_all = 0;
@@ -1244,6 +1245,16 @@ int32_t pa_get_sweep_threads(const pa_ctx* ctx) { return ctx ? ctx->threads : 0;
 pa_status pa_set_sweep_queue(pa_ctx* ctx, int32_t cap) {
     if (!ctx || cap < -1) return PA_ERR_ARG;
     ctx->kp.qcap_limit = cap;
+    if (ctx->graph) {  // the captured step holds the old kernel parameters
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return PA_OK;
+}
+
+pa_status pa_set_wait_test(pa_ctx* ctx, int32_t on) {
+    if (!ctx || (on != 0 && on != 1)) return PA_ERR_ARG;
+    ctx->kp.lb_hold = on;
     if (ctx->graph) {  // the captured step holds the old kernel parameters
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;

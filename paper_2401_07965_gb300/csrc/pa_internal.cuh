@@ -213,6 +213,7 @@ struct KParams {
     const CtlDev* ctl;       // null without a controller
     double alpha;            // partial resampling threshold (< 0: resample every step)
     int qcap_limit;          // sweep: cap on the undecided-site queue (< 0: its full size)
+    int lb_hold;             // test: scan block 0 withholds its prefix (the waits run out)
     int L_all;               // the side L shared by every run of the batch (0 if they differ)
     // 3D kernel plan: one launch per distinct side (n3 = 0: the general kernel)
     int n3;

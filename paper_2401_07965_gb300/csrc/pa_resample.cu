@@ -967,11 +967,13 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 
 // Called by the 32 lanes of warp 0.  Publishes (a0, a1) of block b and returns in
 // (p0, p1) the sums over blocks 0..b-1 (every lane); false if a wait gave up.
+// publish = false (a test of the bounded waits) leaves block b's descriptor unset.
 __device__ bool look_back(LBDesc* d, int b, unsigned long long a0, unsigned long long a1,
-                          uint32_t ep, unsigned long long& p0, unsigned long long& p1) {
+                          uint32_t ep, unsigned long long& p0, unsigned long long& p1,
+                          bool publish = true) {
     const int lane = threadIdx.x & 31;
     const uint32_t FA = 2u * ep + 1u, FI = 2u * ep + 2u;
-    if (lane == 0) {
+    if (lane == 0 && publish) {
         d[b].agg[0] = a0;
         d[b].agg[1] = a1;
         if (b == 0) {
@@ -1019,7 +1021,7 @@ __device__ bool look_back(LBDesc* d, int b, unsigned long long a0, unsigned long
             }
             __nanosleep(64);
         }
-        if (lane == 0 && ok) {
+        if (lane == 0 && ok && publish) {
             d[b].inc[0] = p0 + a0;
             d[b].inc[1] = p1 + a1;
             st_release(&d[b].flag, FI);
@@ -1132,7 +1134,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_resample(KParams p) {
     const uint64_t eg = block_excl_scan(sg, sh, &tg);
     if (threadIdx.x < 32) {
         unsigned long long p0, p1;
-        const bool ok = look_back(r.lb1, b, tf, tg, st->epoch, p0, p1);
+        const bool ok = look_back(r.lb1, b, tf, tg, st->epoch, p0, p1, !(p.lb_hold && b == 0));
         if (threadIdx.x == 0) {
             pre[0] = p0;
             pre[1] = p1;

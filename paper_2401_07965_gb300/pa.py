@@ -36,7 +36,7 @@ EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observable
            "pa_set_graph", "pa_set_controller", "pa_schedule_taken", "pa_mlp_scratch_bytes",
            "pa_mlp_forward", "pa_mlp_gradients", "pa_mlp_adam", "pa_overlap",
            "pa_set_partial_resampling", "pa_weighted_rows", "pa_set_sweep_queue",
-           "pa_run_schedule_taken"]
+           "pa_run_schedule_taken", "pa_set_wait_test"]
 
 
 class pa_lattice(C.Structure):
@@ -173,6 +173,7 @@ def _load():
     lib.pa_mlp_adam.argtypes = [vp, vp, vp, vp, vp, C.c_int32, C.c_float, vp]
     lib.pa_set_sweep_threads.argtypes = [vp, C.c_int32]
     lib.pa_set_sweep_queue.argtypes = [vp, C.c_int32]
+    lib.pa_set_wait_test.argtypes = [vp, C.c_int32]
     lib.pa_get_sweep_threads.argtypes = [vp]
     lib.pa_get_sweep_threads.restype = C.c_int32
     lib.pa_strerror.argtypes = [C.c_int]
@@ -332,6 +333,10 @@ def pa_set_sweep_threads(ctx, threads):
 
 def pa_set_sweep_queue(ctx, cap):
     _check(_lib.pa_set_sweep_queue(ctx, int(cap)), "pa_set_sweep_queue")
+
+
+def pa_set_wait_test(ctx, on):
+    _check(_lib.pa_set_wait_test(ctx, int(on)), "pa_set_wait_test")
 
 
 def pa_get_sweep_threads(ctx) -> int:

@@ -65,6 +65,30 @@ def test_uneven_spin_glass_batch_matches_oracle(rule):
     b.close()
 
 
+@pytest.mark.parametrize("sides", [(4, 6, 8, 10), (4, 6, 8, 10, 12)])
+def test_3d_batch_of_several_sides_matches_oracle(sides):
+    """3D +-J runs of four sides (one launch of the grouped 3D kernel per side, runs of
+    one side interleaved with the others in the run table) and of five sides (more than
+    the grouped kernel's plan holds: the general kernel takes every run); R ragged
+    against each side's replica groups per CTA; beta to 2 in 5 steps, theta = 2."""
+    Rs = (333, 150, 70, 45, 40)
+    runs = []
+    for k, L in enumerate(sides):
+        runs.append({"dim": 3, "L": L, "R": Rs[k], "couplings": ("ea", 3, k)})
+    runs.append({"dim": 3, "L": sides[0], "R": 97, "couplings": ("ea", 3, 9)})
+    betas = np.linspace(0, 2.0, 6)
+    thetas = np.full(5, 2, np.uint32)
+    b = pa.Batch(runs, betas, thetas, "systematic", 23)
+    orcs = _oracle_runs(b, 23, "systematic")
+    _compare(b, orcs, "init")
+    for i in range(5):
+        b.step(1)
+        for o in orcs:
+            assert o.step() == 0
+        _compare(b, orcs, f"step {i + 1}")
+    b.close()
+
+
 @pytest.mark.parametrize("rule", ["systematic", "nearest"])
 def test_uneven_2d_batch_matches_oracle(rule):
     """The weighted-averaging batch shape, scaled down: 2D Ising L=32, four runs of
