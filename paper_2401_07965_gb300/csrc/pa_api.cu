@@ -43,7 +43,8 @@ enum Region {
 
 enum Shared {
     S_RUNS, S_B2R, S_G2R, S_BETA, S_DBETA, S_Q, S_THR, S_THETA, S_IDS, S_WOUT,
-    S_CTL, S_GBETA, S_GTHR, S_GDB, S_GQ, S_PAIRS, S_POV, S_OVACC, S_OVTICK, S_C3, S_COUNT
+    S_CTL, S_GBETA, S_GTHR, S_GDB, S_GQ, S_PAIRS, S_POV, S_OVACC, S_OVTICK, S_C3, S_CLNC,
+    S_COUNT
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -192,6 +193,7 @@ Layout make_layout(const std::vector<RunHost>& runs, int n_steps) {
     size_t nct3 = 0;
     for (const RunHost& h : runs) nct3 += (size_t)h.nct3;
     sz[S_C3] = nct3 * 4;
+    sz[S_CLNC] = (CLN_TAB + 1) * 8;
     size_t o = 0;
     for (int r = 0; r < S_COUNT; ++r) {
         L.shared_off[r] = o;
@@ -569,6 +571,7 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     p.q = (const double*)(base + lay.shared_off[S_Q]);
     p.thr = (const uint32_t*)(base + lay.shared_off[S_THR]);
     p.theta = (const uint32_t*)(base + lay.shared_off[S_THETA]);
+    p.clnc = (const double*)(base + lay.shared_off[S_CLNC]);
     ctx->d_ids = (int32_t*)(base + lay.shared_off[S_IDS]);
     ctx->d_wout = (pa_weighted_obs*)(base + lay.shared_off[S_WOUT]);
     ctx->d_pairs = (int32_t*)(base + lay.shared_off[S_PAIRS]);
@@ -707,6 +710,9 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     up(p.q, q.data(), sizeof(double) * n);
     up(p.thr, thr.data(), sizeof(uint32_t) * 4 * n);
     up(p.theta, ctx->theta.data(), sizeof(uint32_t) * n);
+    double clnc[CLN_TAB + 1];
+    for (int c = 0; c <= CLN_TAB; ++c) clnc[c] = c > 1 ? (double)c * std::log((double)c) : 0.0;
+    up(p.clnc, clnc, sizeof(clnc));
     for (int m = 0; m < M && e == cudaSuccess; ++m) {
         const RunHost& h = ctx->runs[m];
         const RunDesc& r = ctx->desc[m];

@@ -42,55 +42,120 @@ __device__ __forceinline__ float bf_round(float v) {
 
 // --------------------------------------------------------------------------
 // controller step
+//
+// One CTA of 64 threads per run; its time is latency (one thread's FP64
+// division or logarithm costs hundreds of cycles on this part), so the work is
+// spread: each weight row is loaded into the registers of the thread that
+// uses it at entry, the features are formed by threads 0-8 at once, and the
+// step-table entries of every admissible step size are prefetched while the
+// network runs.  Every value is formed by the same operations in the same
+// order as a single thread would, so the results do not change.
 // --------------------------------------------------------------------------
+__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
+
+// sum_k w[k] x[k] over a row of 64 BF16 weights held as 8 uint4, in order, then + bias
+__device__ __forceinline__ float row64(const uint4 (&wr)[8], const float* xv, float bias) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t v[4] = {wr[q].x, wr[q].y, wr[q].z, wr[q].w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            acc = __fadd_rn(acc, __fmul_rn(bf_lo(v[h]), xv[8 * q + 2 * h]));
+            acc = __fadd_rn(acc, __fmul_rn(bf_hi(v[h]), xv[8 * q + 2 * h + 1]));
+        }
+    }
+    return __fadd_rn(acc, bias);
+}
+
 __global__ void __launch_bounds__(64) k_control(KParams p) {
+    static_assert(MLP_HID == 64 && MLP_IN == 8 && MLP_OUT == 2, "row layout of k_control");
     const RunDesc& r = p.runs[blockIdx.x];  // one CTA per run of the batch
     DevState* st = r.st;
     if (st->status != S_OK) return;
     const CtlDev& c = *p.ctl;
     const int i = st->step;
+    const int kg = st->kgrid;
     TraceRow* tr = r.trace + i;
     __shared__ float x[MLP_IN], h1[MLP_HID], h2[MLP_HID], out[MLP_OUT];
+    __shared__ double a5, lnR0;
+    __shared__ double pbeta[CTL_UMAX], pdb[CTL_UMAX], pq[CTL_UMAX];
+    __shared__ uint32_t pthr[CTL_UMAX][4];
     const int t = threadIdx.x;
-    if (t == 0) {
-        const double R = (double)tr->R_i, N = (double)r.N;
-        const double mE = (double)(long long)tr->sumE / R;
-        const double var = ((double)(long long)tr->sumE2 / R - mE * mE) / N;
-        const double th = i > 0 ? (double)r.stheta[i - 1] : 0.0;
-        const double lnR0 = log(fmax((double)r.R, 2.0));
-        x[0] = (float)r.sbeta[i];
-        x[1] = (float)(mE / N);
-        x[2] = (float)(var / 10.0);
-        x[3] = (float)(tr->lnQ / N * 10.0);
-        x[4] = (float)((double)(long long)tr->sumC2 / (R * R));
-        x[5] = (float)((log(R) - tr->c_ln_c / R) / lnR0);
-        x[6] = th > 0 ? (float)((double)tr->accepts / (th * N * R)) : 0.0f;
-        x[7] = (float)r.L / 64.0f;
-        for (int k = 0; k < MLP_IN; ++k) tr->x[k] = x[k];
-    }
-    __syncthreads();
+    // the thread's weight rows (rows of 8 and 64 BF16 values are 16-byte aligned)
     const uint16_t* w = c.w;
-    float acc = 0.0f;
-    for (int k = 0; k < MLP_IN; ++k) acc = __fadd_rn(acc, __fmul_rn(bf(w[OFF_W1 + t * MLP_IN + k]), x[k]));
-    acc = __fadd_rn(acc, bf(w[OFF_B1 + t]));
-    h1[t] = acc > 0.0f ? acc : 0.0f;
-    __syncthreads();
-    acc = 0.0f;
-    for (int k = 0; k < MLP_HID; ++k)
-        acc = __fadd_rn(acc, __fmul_rn(bf(w[OFF_W2 + t * MLP_HID + k]), h1[k]));
-    acc = __fadd_rn(acc, bf(w[OFF_B2 + t]));
-    h2[t] = acc > 0.0f ? acc : 0.0f;
-    __syncthreads();
+    const uint4 w1 = *reinterpret_cast<const uint4*>(w + OFF_W1 + t * MLP_IN);
+    uint4 w2[8], w3[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) w2[q] = reinterpret_cast<const uint4*>(w + OFF_W2 + t * MLP_HID)[q];
     if (t < MLP_OUT) {
-        acc = 0.0f;
-        for (int k = 0; k < MLP_HID; ++k)
-            acc = __fadd_rn(acc, __fmul_rn(bf(w[OFF_W3 + t * MLP_HID + k]), h2[k]));
-        out[t] = __fadd_rn(acc, bf(w[OFF_B3 + t]));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w3[q] = reinterpret_cast<const uint4*>(w + OFF_W3 + t * MLP_HID)[q];
     }
+    const float b1 = bf(w[OFF_B1 + t]), b2 = bf(w[OFF_B2 + t]);
+    const float b3 = t < MLP_OUT ? bf(w[OFF_B3 + t]) : 0.0f;
+
+    // features (R22), one per thread; thread 5's needs ln R_i and ln R (thread 8)
+    {
+        const double R = (double)tr->R_i, N = (double)r.N;
+        if (t == 0) x[0] = (float)r.sbeta[i];
+        if (t == 1 || t == 2) {
+            const double mE = (double)(long long)tr->sumE / R;
+            if (t == 1) {
+                x[1] = (float)(mE / N);
+            } else {
+                const double var = ((double)(long long)tr->sumE2 / R - mE * mE) / N;
+                x[2] = (float)(var / 10.0);
+            }
+        }
+        if (t == 3) x[3] = (float)(tr->lnQ / N * 10.0);
+        if (t == 4) x[4] = (float)((double)(long long)tr->sumC2 / (R * R));
+        if (t == 5) a5 = log(R) - tr->c_ln_c / R;
+        if (t == 6) {
+            const double th = i > 0 ? (double)r.stheta[i - 1] : 0.0;
+            x[6] = th > 0 ? (float)((double)tr->accepts / (th * N * R)) : 0.0f;
+        }
+        if (t == 7) x[7] = (float)r.L / 64.0f;
+        if (t == 8) lnR0 = log(fmax((double)r.R, 2.0));
+    }
+    // the step tables of the admissible next steps u = 1 .. CTL_UMAX (k + u <= K)
+    if (t >= 16 && t < 16 + CTL_UMAX) {
+        const int u = t - 15;
+        if (kg + u <= c.K) {
+            const int kn = kg + u;
+            pbeta[u - 1] = c.beta_grid[kn];
+            pdb[u - 1] = c.dbeta_tab[(size_t)kg * CTL_UMAX + (u - 1)];
+            pq[u - 1] = c.q_tab[(size_t)kg * CTL_UMAX + (u - 1)];
+            for (int m = 0; m < 4; ++m) pthr[u - 1][m] = c.thr_grid[4 * kn + m];
+        }
+    }
+    __syncthreads();
+    if (t == 5) x[5] = (float)(a5 / lnR0);
+    __syncthreads();
+    if (t < MLP_IN) tr->x[t] = x[t];
+    {
+        const uint32_t v[4] = {w1.x, w1.y, w1.z, w1.w};
+        float acc = 0.0f;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            acc = __fadd_rn(acc, __fmul_rn(bf_lo(v[h]), x[2 * h]));
+            acc = __fadd_rn(acc, __fmul_rn(bf_hi(v[h]), x[2 * h + 1]));
+        }
+        acc = __fadd_rn(acc, b1);
+        h1[t] = acc > 0.0f ? acc : 0.0f;
+    }
+    __syncthreads();
+    {
+        const float acc = row64(w2, h1, b2);
+        h2[t] = acc > 0.0f ? acc : 0.0f;
+    }
+    __syncthreads();
+    if (t < MLP_OUT) out[t] = row64(w3, h2, b3);
     __syncthreads();
     if (t != 0) return;
 
-    const int k = st->kgrid;
+    const int k = kg;
     const int D = c.K - k;
     if (D <= 0) {
         st->status = S_DONE;  // beta_f reached: the run is complete
@@ -122,10 +187,10 @@ __global__ void __launch_bounds__(64) k_control(KParams p) {
         if ((long long)th > cap) th = cap > (long long)c.theta_min ? (uint32_t)cap : c.theta_min;
     }
     const int kn = k + u;
-    r.sbeta[i + 1] = c.beta_grid[kn];
-    r.sdbeta[i] = c.dbeta_tab[(size_t)k * CTL_UMAX + (u - 1)];
-    r.sq[i] = c.q_tab[(size_t)k * CTL_UMAX + (u - 1)];
-    for (int m = 0; m < 4; ++m) r.sthr[4 * i + m] = c.thr_grid[4 * kn + m];
+    r.sbeta[i + 1] = pbeta[u - 1];
+    r.sdbeta[i] = pdb[u - 1];
+    r.sq[i] = pq[u - 1];
+    for (int m = 0; m < 4; ++m) r.sthr[4 * i + m] = pthr[u - 1][m];
     r.stheta[i] = th;
     st->kgrid = kn;
     st->sweeps = used + th;

@@ -49,6 +49,7 @@ constexpr int MLP_IN = 8, MLP_HID = 64, MLP_OUT = 2;
 constexpr int MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID +
                            MLP_OUT * MLP_HID + MLP_OUT;
 constexpr int CTL_UMAX = 8;  // largest step in grid units
+constexpr int CLN_TAB = 64;  // family sizes c <= CLN_TAB take c ln c from a table
 
 struct CtlDev {
     uint16_t w[MLP_NPARAM];      // BF16 parameters: W1, b1, W2, b2, W3, b3
@@ -214,6 +215,7 @@ struct KParams {
     double alpha;            // partial resampling threshold (< 0: resample every step)
     int qcap_limit;          // sweep: cap on the undecided-site queue (< 0: its full size)
     int lb_hold;             // test: scan block 0 withholds its prefix (the waits run out)
+    const double* clnc;      // c ln c for c = 0 .. CLN_TAB (0 for c < 2), from the host's log
     int L_all;               // the side L shared by every run of the batch (0 if they differ)
     // 3D kernel plan: one launch per distinct side (n3 = 0: the general kernel)
     int n3;

@@ -782,18 +782,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
     const int j0 = b * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
     // Families stay sorted by slot, so a family is a run of equal values.  The
     // block's slots go to shared memory; each run start finds its end from the
-    // 32-slot masks of run starts, and only the block's last run, which may go on
-    // past the block, searches the array beyond it.  c ln c of small families
-    // comes from a table.
-    constexpr int FTAB = 64;
+    // 32-slot masks of run starts, and warp 0 searches the array beyond the block
+    // for the end of the block's last run, which may go on past it.  c ln c of
+    // small families comes from a table the host computes once.
+    constexpr int FTAB = CLN_TAB;
     __shared__ uint32_t sf[SCAN_CHUNK];
     __shared__ uint32_t smask[SCAN_CHUNK / 32];
     __shared__ double clt[FTAB + 1];
     const uint32_t B0 = b * SCAN_CHUNK;
     const uint32_t nin = B0 < Ri ? min((uint32_t)SCAN_CHUNK, Ri - B0) : 0u;
     if (threadIdx.x == 0) sc2 = 0ull;
-    for (int c = threadIdx.x; c <= FTAB; c += blockDim.x)
-        clt[c] = c > 1 ? __dmul_rn((double)c, log((double)c)) : 0.0;
+    for (int c = threadIdx.x; c <= FTAB; c += blockDim.x) clt[c] = p.clnc[c];
     for (int l = threadIdx.x; l < SCAN_CHUNK; l += blockDim.x)
         sf[l] = (uint32_t)l < nin ? fam[B0 + l] : 0xFFFFFFFFu;
     __syncthreads();
@@ -809,6 +808,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
     __syncthreads();
     double cl = 0.0;
     unsigned long long c2 = 0;
+    __shared__ int slast;  // the block's last run start (-1: no slot in the block)
+    if (threadIdx.x == 0) slast = -1;
+    __syncthreads();
     for (int rnd = 0; rnd < SCAN_CHUNK / SCAN_THREADS; ++rnd) {
         const int l = rnd * SCAN_THREADS + warp * 32 + lane;
         int q = l >> 5;
@@ -816,24 +818,47 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
         if (!((smask[q] >> bit) & 1u)) continue;  // not a run start (or past R_i)
         uint32_t m = bit == 31 ? 0u : (smask[q] & (0xFFFFFFFFu << (bit + 1)));
         while (m == 0u && q + 1 < SCAN_CHUNK / 32) m = smask[++q];
-        uint64_t c;
-        if (m) {
-            c = (uint64_t)(q * 32 + __ffs(m) - 1 - l);
-        } else {  // the block's last run: it may continue past the block
-            uint32_t lo = B0 + nin, hi = Ri;
-            const uint32_t f = sf[l];
-            if (lo < hi && fam[lo] == f) {
-                ++lo;
-                while (lo < hi) {  // first index past the run of f
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (fam[mid] == f) lo = mid + 1;
-                    else hi = mid;
-                }
-            }
-            c = (uint64_t)(lo - (B0 + l));
+        if (!m) {  // the block's last run: it may continue past the block (below)
+            slast = l;
+            continue;
         }
+        const uint64_t c = (uint64_t)(q * 32 + __ffs(m) - 1 - l);
         c2 += c * c;
         if (c > 1) cl = __dadd_rn(cl, c <= FTAB ? clt[c] : __dmul_rn((double)c, log((double)c)));
+    }
+    __syncthreads();
+    // The last run ends at the first slot from B0 + nin on whose family differs
+    // (families are sorted, so "differs" holds from there on): warp 0 finds it by
+    // a 32-way search, each round sampling 32 evenly spaced slots of the interval
+    // that holds the end (at most five rounds below 2^24 slots).
+    if (warp == 0 && slast >= 0) {
+        const uint32_t f = sf[slast];
+        uint32_t lo = B0 + nin, hi = Ri;  // the end lies in [lo, hi]
+        while (hi - lo > 32u) {
+            const uint32_t step = (hi - lo + 31u) / 32u;
+            const uint32_t pos = lo + (uint32_t)lane * step;
+            const bool ne = pos >= hi || fam[pos] != f;
+            const uint32_t bal = __ballot_sync(0xffffffffu, ne);
+            const int k = bal ? __ffs(bal) - 1 : 32;
+            if (k == 0) {
+                hi = lo;
+                break;
+            }
+            const uint32_t nlo = lo + (uint32_t)(k - 1) * step + 1u;
+            if (k < 32) hi = min(hi, lo + (uint32_t)k * step);
+            lo = nlo;
+        }
+        if (lo < hi) {
+            const uint32_t pos = lo + (uint32_t)lane;
+            const bool ne = pos >= hi || fam[pos] != f;
+            const uint32_t bal = __ballot_sync(0xffffffffu, ne);
+            lo = bal ? min(hi, lo + (uint32_t)(__ffs(bal) - 1)) : hi;
+        }
+        if (lane == 0) {
+            const uint64_t c = (uint64_t)(lo - (B0 + (uint32_t)slast));
+            c2 += c * c;
+            if (c > 1) cl = __dadd_rn(cl, c <= FTAB ? clt[c] : __dmul_rn((double)c, log((double)c)));
+        }
     }
     for (int o = 16; o > 0; o >>= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
     if ((threadIdx.x & 31) == 0 && c2) atomicAdd(&sc2, c2);
@@ -1040,9 +1065,11 @@ __device__ __forceinline__ int take_ticket(uint32_t* tick, int* sb) {
 // Copy numbers' exclusive scan (look-back over lb2), the ancestor scatter and the
 // block's sampling-variance partial; the last block sets the new population size
 // (or the capacity error) and resets the tickets.
-__device__ void count_scan_scatter(const KParams& p, const RunDesc& r, DevState* st, int b,
-                                   const uint32_t (&rc)[SCAN_ITEMS], uint64_t* sh, double* sd,
-                                   int* flag_sh) {
+__device__ __forceinline__ void count_scan_scatter(const KParams& p, const RunDesc& r,
+                                                   DevState* st, int b,
+                                                   const uint32_t (&rc)[SCAN_ITEMS], uint64_t* sh,
+                                                   double* sd, int* flag_sh,
+                                                   const uint64_t (&fv)[SCAN_ITEMS], bool have_f) {
     const int i = st->step + 1;
     const int32_t* E = r.E[(i - 1) & 1];
     const int dN = p.d * r.N;
@@ -1069,6 +1096,7 @@ __device__ void count_scan_scatter(const KParams& p, const RunDesc& r, DevState*
     }
     uint64_t o = pre + ex;
     double sv = 0.0;
+#pragma unroll
     for (int e = 0; e < SCAN_ITEMS; ++e) {
         const int j = j0 + e;
         if ((uint32_t)j >= Rprev) break;
@@ -1077,7 +1105,8 @@ __device__ void count_scan_scatter(const KParams& p, const RunDesc& r, DevState*
         for (uint32_t c = 0; c < rc[e]; ++c)
             if (o + c < (uint64_t)r.Rcap) r.anc[o + c] = (uint32_t)j;
         o += rc[e];
-        const double tau = scalbn((double)f_of(j, p, r, st, dN, E, lmin), -FRAC_BITS);
+        const double tau =
+            scalbn((double)(have_f ? fv[e] : f_of(j, p, r, st, dN, E, lmin)), -FRAC_BITS);
         const double dl = __dsub_rn((double)rc[e], tau);
         sv = __dadd_rn(sv, __dmul_rn(dl, dl));
     }
@@ -1153,12 +1182,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_resample(KParams p) {
         usys = philox(0u, DOM_RESAMPLE | (r.run << 8) | RULE_SYSTEMATIC, (uint32_t)i, 0u, p.k0, p.k1).x;
     bool kmax = false;
     uint32_t rc[SCAN_ITEMS];
+    // systematic: labels below the running boundary, carried from item to item
+    uint64_t below = method == M_SYSTEMATIC ? sys_below(cf, r.R, T, usys) : 0ull;
 #pragma unroll 1
     for (int e = 0; e < SCAN_ITEMS; ++e) {
         const int j = j0 + e;
         rc[e] = 0u;
         if ((uint32_t)j >= Rprev) continue;
-        const uint64_t prevC = cf;
         cf += f[e];
         cg += f[e] & ((1ull << FRAC_BITS) - 1);
         uint32_t cnt = 0;
@@ -1169,7 +1199,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_resample(KParams p) {
             cnt = (uint32_t)(f[e] >> FRAC_BITS) +
                   (u40 < (f[e] & ((1ull << FRAC_BITS) - 1)) ? 1u : 0u);
         } else if (method == M_SYSTEMATIC) {
-            cnt = (uint32_t)(sys_below(cf, r.R, T, usys) - sys_below(prevC, r.R, T, usys));
+            const uint64_t bn = sys_below(cf, r.R, T, usys);
+            cnt = (uint32_t)(bn - below);
+            below = bn;
         } else if (method == M_RESIDUAL) {
             r.C[j] = cf;
             r.G[j] = cg;
@@ -1212,7 +1244,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_resample(KParams p) {
         if (threadIdx.x == 0 && b == r.nblk - 1) r.tick[0] = 0u;
         return;
     }
-    count_scan_scatter(p, r, st, b, rc, sh, sd, &okf);
+    count_scan_scatter(p, r, st, b, rc, sh, sd, &okf, f, true);
 }
 
 // multinomial / residual: the copy numbers are complete after k_draws
@@ -1232,7 +1264,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_cscan(KParams p) {
         const int j = j0 + e;
         rc[e] = ((uint32_t)j < Rprev) ? r.counts[j] : 0u;
     }
-    count_scan_scatter(p, r, st, b, rc, sh, sd, &okf);
+    const uint64_t nof[SCAN_ITEMS] = {};
+    count_scan_scatter(p, r, st, b, rc, sh, sd, &okf, nof, false);
 }
 
 // --------------------------------------------------------------------------
