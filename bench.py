@@ -842,6 +842,20 @@ def run_controller(args):
         return 1
     bits = CT.load()
     stream = torch.cuda.Stream()
+    if args.case == "small":
+        # profiling case: two learned runs of the time-to-1e-4 arm (2D Ising L=64,
+        # R=3000, 800-point grid, 2000 sweeps, 512 sweep threads), device time per run
+        ms = []
+        for seed in (11, 12):
+            pop = CT.controlled_run(2, 64, ("ferro",), 3000, np.linspace(0.0, 1.0, 801), 4, 10,
+                                    bits, seed=seed, budget=2000, stream=stream,
+                                    sweep_threads=512)
+            ms.append(_chunked(pa, pop, stream, 800))
+            pop.close()
+        _line("learned schedule, profiling case: 2D Ising L=64, R=3000, 800-point grid, "
+              "2000 sweeps, 2 seeds", float(np.mean(ms)), float(np.sum(ms)), 2, 0,
+              {"unit": "ms per run", "higher_is_better": False})
+        return 0
     rng = np.random.default_rng(2024)
     S = args.seeds
     seeds = range(1, S + 1)

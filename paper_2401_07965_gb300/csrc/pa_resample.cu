@@ -1134,7 +1134,7 @@ __device__ __forceinline__ void count_scan_scatter(const KParams& p, const RunDe
 // look-back over lb1, and the copy numbers of the rules that need no search.
 // FULL (nearest, systematic, Poisson): then the count scan and the scatter too.
 template <bool FULL>
-__global__ void __launch_bounds__(SCAN_THREADS) k_resample(KParams p) {
+__global__ void __launch_bounds__(SCAN_THREADS, 4) k_resample(KParams p) {
     const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
     DevState* st = r.st;
     if (st->status != S_OK) return;
