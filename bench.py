@@ -659,13 +659,16 @@ def accuracy_l64(pa, dev, seeds=(11, 12, 13, 14, 15)):
     """Time to a free energy within 1e-4 per spin of Kaufman's exact value at beta_f = 1 on
     the benchmark lattice (2D Ising L=64), systematic rule, worst of 5 seeds, device time
     per run (CUDA events, graph replay): the least time over
-      plain:      200 equal steps, R in {3000, 10^4, 3 10^4, 10^5} x theta in {2, 5, 10};
+      plain:      200 equal steps, R in {3000, R1, 10^4, 3 10^4, 10^5} x theta in {2, 5, 10};
       plain800:   800 equal steps (the learned schedule's grid) at 1000 or 2000 sweeps in
-                  all, R in {3000, 10^4, 3 10^4};
-      batched:    M in {4, 8, 12} runs of 2500 replicas or 4 of 7500 in one batch, 200
-                  steps, theta in {2, 5, 10}, combined by Eq. (weighted-averages);
-      learned:    the learned controller on the 800-point grid, budgets 500, 1000 or 2000
-                  sweeps, R in {3000, 10^4, 3 10^4}."""
+                  all, R in {3000, R1, 10^4, 3 10^4};
+      batched:    M in {4, 8, 12} runs of 2500 replicas, 4 of 7500, or 4 and 8 of R1/4 in
+                  one batch, 200 steps, theta in {2, 5, 10}, combined by Eq.
+                  (weighted-averages);
+      learned:    the learned controller on the 800-point grid, budgets 500, 1000, 1500 or
+                  2000 sweeps, R in {3000, R1, 10^4, 3 10^4}.
+    R1 = 32 x the GPU's SM count (4864 on a GB300): one replica group per SM, the largest
+    population whose sweep is one wave of CTAs."""
     import torch
     from paper_2401_07965_gb300 import controller as CT
     stream = torch.cuda.Stream(dev)
@@ -674,12 +677,15 @@ def accuracy_l64(pa, dev, seeds=(11, 12, 13, 14, 15)):
     out = {"target_per_spin": 1e-4, "seeds": len(seeds), "lattice": "2D Ising L=64, beta 0->1",
            "what": "device ms per run of the cheapest configuration whose worst-seed |f - f_exact| "
                    "per spin is <= 1e-4 (Kaufman's exact finite-lattice value)"}
+    R1 = 32 * torch.cuda.get_device_properties(dev).multi_processor_count
+    out["R1"] = R1
     plain = [_plain_point(pa, Lx, 200, R, np.full(200, th, np.uint32), seeds, stream, exact)
-             for R in (3000, 10000, 30000, 100000) for th in (2, 5, 10)]
+             for R in (3000, R1, 10000, 30000, 100000) for th in (2, 5, 10)]
     p800 = [_plain_point(pa, Lx, 800, R, _spread_thetas(800, sw), seeds, stream, exact)
-            for R in (3000, 10000, 30000) for sw in (1000, 2000)]
+            for R in (3000, R1, 10000, 30000) for sw in (1000, 2000)]
     batched = [_batch_point(pa, Lx, 200, M, Rm, th, seeds, stream, exact)
-               for M, Rm in ((4, 2500), (8, 2500), (12, 2500), (4, 7500)) for th in (2, 5, 10)]
+               for M, Rm in ((4, 2500), (8, 2500), (12, 2500), (4, 7500), (4, R1 // 4),
+                             (8, R1 // 4)) for th in (2, 5, 10)]
     out["plain"] = {"best": _best(plain), "grid": plain}
     out["plain800"] = {"best": _best(p800), "grid": p800}
     out["batched"] = {"best": _best(batched), "grid": batched,
@@ -688,7 +694,7 @@ def accuracy_l64(pa, dev, seeds=(11, 12, 13, 14, 15)):
     if os.path.exists(CT.WEIGHTS):
         bits = CT.load()
         learned = [_learned_point(pa, CT, Lx, 800, R, bud, seeds, stream, exact, bits)
-                   for R in (3000, 10000, 30000) for bud in (500, 1000, 2000)]
+                   for R in (3000, R1, 10000, 30000) for bud in (500, 1000, 1500, 2000)]
         out["learned"] = {"best": _best(learned), "grid": learned}
     cands = [v["best"] for k, v in out.items() if isinstance(v, dict) and v.get("best")]
     bp = [out[k]["best"] for k in ("plain", "plain800") if out[k]["best"]]

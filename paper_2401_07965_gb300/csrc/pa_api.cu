@@ -373,11 +373,8 @@ pa_status enqueue_step(pa_ctx* ctx, int64_t* launches) {
     PA_CUDA(launch_resample(ctx->kp, ctx->stream, launches));
     PA_CUDA(launch_sweep(ctx->kp, ctx->threads, ctx->stream));
     if (launches) *launches += 1;
+    // the family kernel's last CTA of each run also takes the controller's decision
     PA_CUDA(launch_family_finish(ctx->kp, 0, ctx->stream, launches));
-    if (ctx->controlled) {
-        PA_CUDA(launch_control(ctx->kp, ctx->stream));
-        if (launches) *launches += 1;
-    }
     return PA_OK;
 }
 
@@ -607,6 +604,7 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
         r.nlev = h.nlev;
         r.parity = h.parity;
         r.R = h.R;
+        r.lnR = std::log(std::max((double)h.R, 2.0));
         r.Rcap = h.Rcap;
         if (!make_magic(h.L, h.N, &r.magicL, &r.shiftL)) {
             pa_destroy(ctx);
@@ -799,10 +797,6 @@ pa_status pa_step(pa_ctx* ctx, int32_t n) {
             ctx->launches += 1;
             PA_CUDA(cudaEventRecord(b, ctx->stream));
             PA_CUDA(launch_family_finish(ctx->kp, 0, ctx->stream, &ctx->launches));
-            if (ctx->controlled) {
-                PA_CUDA(launch_control(ctx->kp, ctx->stream));
-                ctx->launches += 1;
-            }
         } else {
             const pa_status s = enqueue_step(ctx, &ctx->launches);
             if (s != PA_OK) return s;

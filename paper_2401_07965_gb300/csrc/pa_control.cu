@@ -7,195 +7,34 @@
 // Outputs: s, the step size relative to the average remaining step, and t,
 // the sweeps relative to the planned sweeps per step.
 //
-// Inference runs after every temperature step in one CTA (k_control): it
-// reads the step's population sums, forms the features, evaluates the
-// network, and writes the next step's entries of the step tables (beta on the
-// schedule grid, dbeta, q = exp(-4 dbeta), Metropolis thresholds, theta) from
-// tables precomputed on the host, so the PA step itself is unchanged and stays
-// bit-exact.  With a non-finite or out-of-range output, or with the network
-// switched off, the plain step (plain_units, plain_theta) is taken.
+// Inference (pa_control.cuh) runs once per run when the controller is switched
+// on (k_control) and then after every temperature step in the family kernel's
+// last CTA of the run: it writes the next step's entries of the step tables
+// from tables precomputed on the host, so the PA step itself is unchanged and
+// stays bit-exact.
 #include <cmath>
 #include <cuda_bf16.h>
 
 #include "../../include/pa.h"
-#include "pa_internal.cuh"
+#include "pa_control.cuh"
 
 namespace pa {
 
 namespace {
-constexpr int OFF_W1 = 0;
-constexpr int OFF_B1 = OFF_W1 + MLP_HID * MLP_IN;
-constexpr int OFF_W2 = OFF_B1 + MLP_HID;
-constexpr int OFF_B2 = OFF_W2 + MLP_HID * MLP_HID;
-constexpr int OFF_W3 = OFF_B2 + MLP_HID;
-constexpr int OFF_B3 = OFF_W3 + MLP_OUT * MLP_HID;
 constexpr int ROWS = 32;  // rows per CTA of the training kernels
 }  // namespace
-
-__device__ __forceinline__ float bf(uint16_t v) {
-    return __uint_as_float(((uint32_t)v) << 16);
-}
 
 __device__ __forceinline__ float bf_round(float v) {
     return __bfloat162float(__float2bfloat16_rn(v));
 }
 
 // --------------------------------------------------------------------------
-// controller step
-//
-// One CTA of 64 threads per run; its time is latency (one thread's FP64
-// division or logarithm costs hundreds of cycles on this part), so the work is
-// spread: each weight row is loaded into the registers of the thread that
-// uses it at entry, the features are formed by threads 0-8 at once, and the
-// step-table entries of every admissible step size are prefetched while the
-// network runs.  Every value is formed by the same operations in the same
-// order as a single thread would, so the results do not change.
+// controller step: the first decision of a run (at pa_set_controller); after
+// every step the family kernel's last CTA of the run makes it
 // --------------------------------------------------------------------------
-__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
-__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
-
-// sum_k w[k] x[k] over a row of 64 BF16 weights held as 8 uint4, in order, then + bias
-__device__ __forceinline__ float row64(const uint4 (&wr)[8], const float* xv, float bias) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const uint32_t v[4] = {wr[q].x, wr[q].y, wr[q].z, wr[q].w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            acc = __fadd_rn(acc, __fmul_rn(bf_lo(v[h]), xv[8 * q + 2 * h]));
-            acc = __fadd_rn(acc, __fmul_rn(bf_hi(v[h]), xv[8 * q + 2 * h + 1]));
-        }
-    }
-    return __fadd_rn(acc, bias);
-}
-
 __global__ void __launch_bounds__(64) k_control(KParams p) {
-    static_assert(MLP_HID == 64 && MLP_IN == 8 && MLP_OUT == 2, "row layout of k_control");
     const RunDesc& r = p.runs[blockIdx.x];  // one CTA per run of the batch
-    DevState* st = r.st;
-    if (st->status != S_OK) return;
-    const CtlDev& c = *p.ctl;
-    const int i = st->step;
-    const int kg = st->kgrid;
-    TraceRow* tr = r.trace + i;
-    __shared__ float x[MLP_IN], h1[MLP_HID], h2[MLP_HID], out[MLP_OUT];
-    __shared__ double a5, lnR0;
-    __shared__ double pbeta[CTL_UMAX], pdb[CTL_UMAX], pq[CTL_UMAX];
-    __shared__ uint32_t pthr[CTL_UMAX][4];
-    const int t = threadIdx.x;
-    // the thread's weight rows (rows of 8 and 64 BF16 values are 16-byte aligned)
-    const uint16_t* w = c.w;
-    const uint4 w1 = *reinterpret_cast<const uint4*>(w + OFF_W1 + t * MLP_IN);
-    uint4 w2[8], w3[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) w2[q] = reinterpret_cast<const uint4*>(w + OFF_W2 + t * MLP_HID)[q];
-    if (t < MLP_OUT) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) w3[q] = reinterpret_cast<const uint4*>(w + OFF_W3 + t * MLP_HID)[q];
-    }
-    const float b1 = bf(w[OFF_B1 + t]), b2 = bf(w[OFF_B2 + t]);
-    const float b3 = t < MLP_OUT ? bf(w[OFF_B3 + t]) : 0.0f;
-
-    // features (R22), one per thread; thread 5's needs ln R_i and ln R (thread 8)
-    {
-        const double R = (double)tr->R_i, N = (double)r.N;
-        if (t == 0) x[0] = (float)r.sbeta[i];
-        if (t == 1 || t == 2) {
-            const double mE = (double)(long long)tr->sumE / R;
-            if (t == 1) {
-                x[1] = (float)(mE / N);
-            } else {
-                const double var = ((double)(long long)tr->sumE2 / R - mE * mE) / N;
-                x[2] = (float)(var / 10.0);
-            }
-        }
-        if (t == 3) x[3] = (float)(tr->lnQ / N * 10.0);
-        if (t == 4) x[4] = (float)((double)(long long)tr->sumC2 / (R * R));
-        if (t == 5) a5 = log(R) - tr->c_ln_c / R;
-        if (t == 6) {
-            const double th = i > 0 ? (double)r.stheta[i - 1] : 0.0;
-            x[6] = th > 0 ? (float)((double)tr->accepts / (th * N * R)) : 0.0f;
-        }
-        if (t == 7) x[7] = (float)r.L / 64.0f;
-        if (t == 8) lnR0 = log(fmax((double)r.R, 2.0));
-    }
-    // the step tables of the admissible next steps u = 1 .. CTL_UMAX (k + u <= K)
-    if (t >= 16 && t < 16 + CTL_UMAX) {
-        const int u = t - 15;
-        if (kg + u <= c.K) {
-            const int kn = kg + u;
-            pbeta[u - 1] = c.beta_grid[kn];
-            pdb[u - 1] = c.dbeta_tab[(size_t)kg * CTL_UMAX + (u - 1)];
-            pq[u - 1] = c.q_tab[(size_t)kg * CTL_UMAX + (u - 1)];
-            for (int m = 0; m < 4; ++m) pthr[u - 1][m] = c.thr_grid[4 * kn + m];
-        }
-    }
-    __syncthreads();
-    if (t == 5) x[5] = (float)(a5 / lnR0);
-    __syncthreads();
-    if (t < MLP_IN) tr->x[t] = x[t];
-    {
-        const uint32_t v[4] = {w1.x, w1.y, w1.z, w1.w};
-        float acc = 0.0f;
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            acc = __fadd_rn(acc, __fmul_rn(bf_lo(v[h]), x[2 * h]));
-            acc = __fadd_rn(acc, __fmul_rn(bf_hi(v[h]), x[2 * h + 1]));
-        }
-        acc = __fadd_rn(acc, b1);
-        h1[t] = acc > 0.0f ? acc : 0.0f;
-    }
-    __syncthreads();
-    {
-        const float acc = row64(w2, h1, b2);
-        h2[t] = acc > 0.0f ? acc : 0.0f;
-    }
-    __syncthreads();
-    if (t < MLP_OUT) out[t] = row64(w3, h2, b3);
-    __syncthreads();
-    if (t != 0) return;
-
-    const int k = kg;
-    const int D = c.K - k;
-    if (D <= 0) {
-        st->status = S_DONE;  // beta_f reached: the run is complete
-        return;
-    }
-    const uint32_t used = st->sweeps;
-    const uint32_t Brem = c.budget > used ? c.budget - used : 0u;
-    const float s = out[0], tt = out[1];
-    const bool ok = c.use_mlp && s == s && tt == tt && s >= 0.05f && s <= 20.0f && tt >= 0.05f &&
-                    tt <= 20.0f;
-    int u;
-    uint32_t th;
-    if (ok) {
-        const float nrem = __fdiv_rn((float)Brem, c.theta_c);       // planned remaining steps
-        const float ubar = __fdiv_rn((float)D, fmaxf(nrem, 1.0f));  // their average size
-        const float uf = rintf(__fmul_rn(s, ubar));
-        u = (int)fminf(fmaxf(uf, 1.0f), (float)c.u_max);
-        const float tf = rintf(__fmul_rn(tt, c.theta_c));
-        th = (uint32_t)fminf(fmaxf(tf, (float)c.theta_min), (float)c.theta_max);
-    } else {
-        u = c.plain_units;
-        th = c.plain_theta;
-    }
-    if (u > D) u = D;
-    if (ok) {
-        // keep theta_min sweeps for each of the fewest steps that still reach beta_f
-        const int need = (D - u + c.u_max - 1) / c.u_max;
-        const long long cap = (long long)Brem - (long long)c.theta_min * need;
-        if ((long long)th > cap) th = cap > (long long)c.theta_min ? (uint32_t)cap : c.theta_min;
-    }
-    const int kn = k + u;
-    r.sbeta[i + 1] = pbeta[u - 1];
-    r.sdbeta[i] = pdb[u - 1];
-    r.sq[i] = pq[u - 1];
-    for (int m = 0; m < 4; ++m) r.sthr[4 * i + m] = pthr[u - 1][m];
-    r.stheta[i] = th;
-    st->kgrid = kn;
-    st->sweeps = used + th;
-    tr->u_next = u;
-    tr->theta_next = th;
+    control_after_step(p, r, r.st);
 }
 
 cudaError_t launch_control(const KParams& p, cudaStream_t s) {

@@ -160,6 +160,7 @@ struct RunDesc {
     uint32_t grp0;           // its first CTA in the flattened sweep grid (= slot_base / 32)
     uint32_t run;            // run index
     uint32_t cta0;           // 3D kernel: its first CTA in the launch for its side
+    double lnR;              // ln max(R, 2), from the host's log (the controller's entropy scale)
     uint32_t* spins[2];
     int32_t* E[2];
     uint32_t* fam[2];

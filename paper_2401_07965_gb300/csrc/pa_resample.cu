@@ -21,7 +21,7 @@
 // and its weight is rescaled by a power of two (k_family).
 #include <climits>
 
-#include "pa_internal.cuh"
+#include "pa_control.cuh"
 
 namespace pa {
 
@@ -765,9 +765,10 @@ template <bool PARTIAL>
 __device__ void finish_run(const KParams& p, const RunDesc& r, DevState* st, int mode, double* a,
                            double* b, double* ws);
 
-// PARTIAL: partial resampling (weighted sums); a separate instance keeps the
-// registers of the plain step's kernel low
-template <bool PARTIAL>
+// PARTIAL: partial resampling (weighted sums); CTL: the run's last CTA then
+// takes the learned controller's decision for the next step.  Separate
+// instances keep the registers of the plain step's kernel low.
+template <bool PARTIAL, bool CTL>
 __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
     const RunDesc& r = p.runs[p.blk2run[blockIdx.x]];
     const uint32_t b = blockIdx.x - r.blk0;
@@ -913,6 +914,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_family(KParams p, int mode) {
     if (threadIdx.x == 0) r.tick[1] = 0u;
     __threadfence();
     finish_run<PARTIAL>(p, r, st, mode, fa, fb, sd);
+    if (CTL && mode == 0) {
+        __syncthreads();  // the trace row and the step count are written
+        control_after_step(p, r, st);
+    }
 }
 
 // fixed-order sums of the run's per-block partials, close the step (one CTA of
@@ -1308,8 +1313,9 @@ cudaError_t launch_partial_init(const KParams& p, cudaStream_t s) {
 }
 
 cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int64_t* launches) {
-    if (p.alpha >= 0.0) k_family<true><<<p.nblk_total, SCAN_THREADS, 0, s>>>(p, mode);
-    else k_family<false><<<p.nblk_total, SCAN_THREADS, 0, s>>>(p, mode);
+    if (p.alpha >= 0.0) k_family<true, false><<<p.nblk_total, SCAN_THREADS, 0, s>>>(p, mode);
+    else if (p.ctl) k_family<false, true><<<p.nblk_total, SCAN_THREADS, 0, s>>>(p, mode);
+    else k_family<false, false><<<p.nblk_total, SCAN_THREADS, 0, s>>>(p, mode);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
