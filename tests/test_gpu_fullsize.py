@@ -76,6 +76,12 @@ def test_full_size_step_against_oracle(rule, k):
     assert np.array_equal(anc, np.repeat(np.arange(len(counts), dtype=np.uint32), counts))
     fam = g.families()
     assert np.array_equal(fam, fam_pre[anc])
+    # family statistics of the new population (families span many scan blocks at
+    # this size, late in the run some of them thousands of slots)
+    _, c = np.unique(fam, return_counts=True)
+    assert obs["sumC2"] == int((c.astype(np.int64) ** 2).sum())
+    pf = c / c.sum()
+    assert math.isclose(obs["entropy"], float(-(pf * np.log(pf)).sum()), rel_tol=1e-9)
     words, E = g.spins_words(), g.energies()
     J = O.ferro_couplings(2, L)
     for d in rng.choice(obs["R_i"], 12, replace=False):
