@@ -94,6 +94,50 @@ def test_full_size_step_against_oracle(rule, k):
     g.close()
 
 
+@pytest.mark.parametrize("rule", ["systematic", "nearest"])
+def test_largest_population_step_against_oracle(rule):
+    """The largest population the 2^-40 fixed-point weights allow (R and R_cap below 2^24):
+    R = 2^24 - 1 for the fixed-size rule; for the nearest-integer rule the largest R whose
+    default capacity stays below 2^24.  2D Ising L=16 (a 32-byte row per replica, half a GB
+    per spin buffer).  After two temperature steps, the third step's copy counts and ln Q
+    equal the oracle's on the GPU's own pre-step energies, the counts sum to R_i, the
+    ancestors follow from them, and sampled replicas swept by the oracle match bit for bit."""
+    L, theta, seed, n = 16, 2, 5, 50
+    rmax = (1 << 24) - 1
+    R = rmax
+    if rule == "nearest":
+        while pa.default_capacity(R, rule) > rmax:
+            R -= 1024
+    betas = np.linspace(0.0, 0.8, n + 1)
+    thetas = np.full(n, theta, np.uint32)
+    g = pa.Population(2, L, R, betas, thetas, rule, seed)
+    g.step(2)
+    E_pre, words_pre = g.energies(), g.spins_words()
+    g.step(1)
+    i = 3
+    obs = g.observables()
+    ref = O.resample(E_pre, R, betas[i] - betas[i - 1], O.RESAMPLERS[rule], seed, i)
+    assert ref["status"] == 0
+    counts = g.counts()
+    assert np.array_equal(counts, ref["counts"])
+    assert obs["R_i"] == ref["R_new"] == int(counts.sum(dtype=np.int64))
+    assert math.isclose(obs["lnQ"], ref["lnQ"], rel_tol=1e-12)
+    anc = g.ancestors()
+    assert np.array_equal(anc, np.repeat(np.arange(len(counts), dtype=np.uint32), counts))
+    words, E = g.spins_words(), g.energies()
+    J = O.ferro_couplings(2, L)
+    N = L * L
+    rng = np.random.default_rng(3)
+    for d in list(rng.choice(obs["R_i"], 6, replace=False)) + [obs["R_i"] - 1]:
+        parent = words_pre[anc[d]]
+        bits = ((parent[:, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(-1)[:N]
+        sig = (1 - 2 * bits.astype(np.int8)).astype(np.int8)
+        s2, E2, _ = O.sweeps(2, L, J, sig, seed, i, int(d), theta, betas[i])
+        assert np.array_equal(words[d], O.pack_spins(s2[None])[0]), (rule, d)
+        assert E[d] == E2
+    g.close()
+
+
 def _curand_lib():
     out = os.path.join(tempfile.gettempdir(), f"philox_curand_ref_{os.getpid()}.so")
     if not os.path.exists(out):
