@@ -718,6 +718,8 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
         std::memset(&st0, 0, sizeof(st0));
         st0.R_cur = h.R;
         st0.R_prev = h.R;
+        st0.hlo = 0x7FFFFFFF;
+        st0.hhi = -1;
         up(r.jbits, h.jb.data(), h.jb.size());
         up(r.st, &st0, sizeof(st0));
         if (e == cudaSuccess) e = cudaMemsetAsync(r.hist, 0, (size_t)h.nlev * 4, ctx->stream);
@@ -974,6 +976,8 @@ pa_status pa_set_state(pa_ctx* ctx, const uint32_t* spins, const uint32_t* famil
     st.step = step;
     st.R_cur = R_i;
     st.R_prev = R_i;
+    st.hlo = 0x7FFFFFFF;
+    st.hhi = -1;
     st.sum_lnQ = sum_lnQ;
     PA_CUDA(cudaMemcpy(r.st, &st, sizeof(st), cudaMemcpyHostToDevice));
     PA_CUDA(cudaMemset(r.hist, 0, (size_t)h.nlev * 4));

@@ -117,6 +117,7 @@ struct DevState {
     double S_new;      // partial resampling: sum of the new weights
     uint32_t epoch;    // resampling steps taken (tags the look-back descriptors)
     int32_t kmax;      // a Poisson inversion of this step hit its limit
+    int32_t hlo, hhi;  // lowest / highest histogram level filled since the last reweighting
 };
 
 // Look-back descriptor of one scan block (single-pass scans of the resampling

@@ -178,40 +178,26 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
     DevState* st = r.st;
     if (st->status != S_OK) return;
     constexpr int TREE_SMEM = 2048;
-    // tree and weights; before the tree is built, the level counts (cached when
-    // the nlev 32-bit counts fit in its 4 TREE_SMEM words)
+    // tree and weights; before the tree is built, the counts of the K occupied
+    // levels (cached when they fit in its 4 TREE_SMEM words)
     __shared__ double tw[2 * TREE_SMEM];
     double* tsm = tw;
     double* wsm = tw + TREE_SMEM;
     uint32_t* hc = reinterpret_cast<uint32_t*>(tw);
-    __shared__ int smin[32], smax[32];
     __shared__ double qsq[32], S_sh, lnS_sh, lnR_sh;
     const int i = st->step + 1;
     const uint32_t Rprev = st->R_cur;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = (int)(blockDim.x >> 5);
-    const bool cached = r.nlev <= 4 * TREE_SMEM;
-    int lo = INT_MAX, hi = -1;
-#pragma unroll 4
-    for (int l = threadIdx.x; l < r.nlev; l += blockDim.x) {
-        const uint32_t c = r.hist[l];
-        if (cached) hc[l] = c;
-        if (c) {
-            lo = min(lo, l);
-            hi = max(hi, l);
-        }
-    }
-    lo = __reduce_min_sync(0xffffffffu, lo);
-    hi = __reduce_max_sync(0xffffffffu, hi);
-    if (lane == 0) {
-        smin[warp] = lo;
-        smax[warp] = hi;
-    }
-    __syncthreads();
-    lo = __reduce_min_sync(0xffffffffu, lane < nwarps ? smin[lane] : INT_MAX);
-    hi = __reduce_max_sync(0xffffffffu, lane < nwarps ? smax[lane] : -1);
+    // the occupied level range, recorded by the kernels that filled the histogram
+    // (the lowest and highest level any replica took)
+    const int lo = st->hlo, hi = st->hhi;
     const int lmin = lo;
-    const int K = hi - lo + 1;
+    const int K = hi >= lo ? hi - lo + 1 : 0;
+    const bool cached = K <= 4 * TREE_SMEM;
+    if (cached)
+        for (int k = threadIdx.x; k < K; k += blockDim.x) hc[k] = r.hist[lmin + k];
+    __syncthreads();
     int P = 1;
     while (P < K) P <<= 1;
     const double q = r.sq[i - 1];
@@ -230,8 +216,8 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
     uint32_t n0 = 0u, n1 = 0u;
     if (in_smem) {
         const int k0 = threadIdx.x, k1 = threadIdx.x + blockDim.x;
-        if (k0 < K) n0 = cached ? hc[lmin + k0] : r.hist[lmin + k0];
-        if (k1 < K) n1 = cached ? hc[lmin + k1] : r.hist[lmin + k1];
+        if (k0 < K) n0 = cached ? hc[k0] : r.hist[lmin + k0];
+        if (k1 < K) n1 = cached ? hc[k1] : r.hist[lmin + k1];
     }
     __syncthreads();  // qsq written; the count cache is free for the tree
     if (p.alpha >= 0.0) {
@@ -244,6 +230,8 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
             st->R_prev = Rprev;
             st->lmin = (uint32_t)lmin;
             st->K = (uint32_t)K;
+            st->hlo = 0x7FFFFFFF;  // the histogram is empty again
+            st->hhi = -1;
             TraceRow* tr = r.trace + i;
             tr->c_ln_c = 0.0;
             tr->sv_sum = 0.0;
@@ -345,6 +333,8 @@ __global__ void __launch_bounds__(1024) k_weights(KParams p) {
         st->R_prev = Rprev;
         st->lmin = (uint32_t)lmin;
         st->K = (uint32_t)K;
+        st->hlo = 0x7FFFFFFF;  // the histogram is empty again
+        st->hhi = -1;
         st->sum_lnQ = __dadd_rn(st->sum_lnQ, lnQ);
         TraceRow* tr = r.trace + i;
         tr->lnQ = lnQ;

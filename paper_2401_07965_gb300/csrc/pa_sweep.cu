@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
 
     if (warp == 0) {
         long long e = 0, e2 = 0, am = 0, m2 = 0;
+        int lvmin = 0x7FFFFFFF, lvmax = -1;  // the warp's histogram levels
         if (valid) {
             const int32_t Uv = sU[lane];
             const int32_t E = 2 * Uv - D * N;
@@ -420,6 +421,7 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
             r.E[i & 1][base + lane] = E;
             r.M[base + lane] = M;
             atomicAdd(&r.hist[Uv >> 1], 1u);
+            lvmin = lvmax = Uv >> 1;
             e = E;
             e2 = (long long)E * E;
             am = M < 0 ? -M : M;
@@ -430,6 +432,12 @@ __global__ void __launch_bounds__(NT) k_group(KParams p, int mode) {
             e2 += __shfl_xor_sync(0xffffffffu, e2, o);
             am += __shfl_xor_sync(0xffffffffu, am, o);
             m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+        }
+        lvmin = __reduce_min_sync(0xffffffffu, lvmin);
+        lvmax = __reduce_max_sync(0xffffffffu, lvmax);
+        if (lane == 0 && lvmax >= 0) {  // the occupied level range for the reweighting
+            atomicMin(&r.st->hlo, lvmin);
+            atomicMax(&r.st->hhi, lvmax);
         }
         if (lane == 0) {
             TraceRow* tr = r.trace + i;

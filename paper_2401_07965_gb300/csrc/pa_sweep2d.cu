@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
         }
         // the thread's place in the walk: column slot xi of rows y0, y0 + RP, ...
         int y0, xi;
-        if (TPR >= 16) {
+        if constexpr (TPR >= 16) {
             constexpr int CH = TPR / 16;
             y0 = 2 * (warp / CH) + ((threadIdx.x >> 4) & 1);
             xi = 16 * (warp % CH) + (threadIdx.x & 15);
@@ -452,6 +452,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
 
     if (warp == 0) {
         long long e = 0, e2 = 0, am = 0, m2 = 0;
+        int lvmin = 0x7FFFFFFF, lvmax = -1;  // the warp's histogram levels
         if (valid) {
             const int32_t Uv = sU[lane];
             const int32_t E = 2 * Uv - 2 * N;
@@ -459,6 +460,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
             r.E[i & 1][base + lane] = E;
             r.M[base + lane] = M;
             atomicAdd(&r.hist[Uv >> 1], 1u);
+            lvmin = lvmax = Uv >> 1;
             e = E;
             e2 = (long long)E * E;
             am = M < 0 ? -M : M;
@@ -469,6 +471,12 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
             e2 += __shfl_xor_sync(0xffffffffu, e2, o);
             am += __shfl_xor_sync(0xffffffffu, am, o);
             m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+        }
+        lvmin = __reduce_min_sync(0xffffffffu, lvmin);
+        lvmax = __reduce_max_sync(0xffffffffu, lvmax);
+        if (lane == 0 && lvmax >= 0) {  // the occupied level range for the reweighting
+            atomicMin(&r.st->hlo, lvmin);
+            atomicMax(&r.st->hhi, lvmax);
         }
         if (lane == 0) {
             TraceRow* tr = r.trace + i;

@@ -517,6 +517,7 @@ __global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* c
     for (int g = warp; g < G; g += NW) {
         const uint32_t slot = (gfirst + g) * 32u + lane;
         long long e = 0, e2 = 0, am = 0, m2 = 0;
+        int lvmin = 0x7FFFFFFF, lvmax = -1;  // the warp's histogram levels
         if (slot < R) {
             const int32_t Uv = sU[g][lane];
             const int32_t E = 2 * Uv - 3 * N;
@@ -524,6 +525,7 @@ __global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* c
             r.E[i & 1][slot] = E;
             r.M[slot] = M;
             atomicAdd(&r.hist[Uv >> 1], 1u);
+            lvmin = lvmax = Uv >> 1;
             e = E;
             e2 = (long long)E * E;
             am = M < 0 ? -M : M;
@@ -534,6 +536,12 @@ __global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* c
             e2 += __shfl_xor_sync(0xffffffffu, e2, o);
             am += __shfl_xor_sync(0xffffffffu, am, o);
             m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+        }
+        lvmin = __reduce_min_sync(0xffffffffu, lvmin);
+        lvmax = __reduce_max_sync(0xffffffffu, lvmax);
+        if (lane == 0 && lvmax >= 0) {  // the occupied level range for the reweighting
+            atomicMin(&r.st->hlo, lvmin);
+            atomicMax(&r.st->hhi, lvmax);
         }
         if (lane == 0 && (e | e2 | am | m2)) {
             TraceRow* tr = r.trace + i;
