@@ -250,6 +250,17 @@ int32_t pa_get_sweep_threads(const pa_ctx *ctx);
  * PA_ERR_ARG for cap < -1. */
 pa_status pa_set_sweep_queue(pa_ctx *ctx, int32_t cap);
 
+/* Launch configuration of the grouped 3D sweep kernel (Sec. 2 step 3 for 3D
+ * lattices of even side 4..16): a CTA holds a number of replica groups that
+ * depends on the side; mult = 2 doubles it (fewer, larger CTAs), mult = 1 is
+ * the default.  Results do not depend on it; the package's autotuner times both.
+ * A context whose runs do not use the grouped kernel accepts mult = 1 only.
+ * Synchronises the context's stream.  PA_ERR_ARG for other values,
+ * PA_ERR_STATE after an earlier device error.  pa_get_sweep_groups returns the
+ * multiple in use (1 without the grouped kernel). */
+pa_status pa_set_sweep_groups(pa_ctx *ctx, int32_t mult);
+int32_t pa_get_sweep_groups(const pa_ctx *ctx);
+
 /* Test hook of the failure path (no counterpart in the paper).  The scans of the
  * copy numbers (Sec. 2 step 2) are single-pass: a block waits, by a bounded
  * spin, for the prefix its predecessor publishes.  With on = 1 the first block

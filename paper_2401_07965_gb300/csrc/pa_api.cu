@@ -153,7 +153,7 @@ pa_status make_runs(const pa_run_spec* specs, int M, int method, std::vector<Run
         if (h.Rcap > MAX_POPULATION) return PA_ERR_LIMIT;
         h.nblk = (int)((h.Rcap + SCAN_CHUNK - 1) / SCAN_CHUNK);
         h.ngrp = (int)((h.Rcap + 31) / 32);
-        h.g3 = (*d == 3) ? sweep3d_groups(h.L) : 0;
+        h.g3 = (*d == 3) ? sweep3d_groups(h.L, 1) : 0;
         h.nct3 = h.g3 ? (h.ngrp + h.g3 - 1) / h.g3 : 0;
         h.ensemble = s.ensemble;
         h.parity = 0;
@@ -368,6 +368,30 @@ void fill_obs(const pa_ctx* ctx, int run, const TraceRow& t, int step, pa_obs* o
     o->theta_next = t.theta_next;
 }
 
+// The grouped 3D kernel's CTA plan for group multiple gm: for each distinct side,
+// the CTAs of its runs in run order (the CTA -> run map, from p.c3map[0] on, and
+// each run's first CTA); the side's groups per CTA are its base count times gm.
+void plan3d(pa_ctx* ctx, int gm, std::vector<uint32_t>& c3) {
+    KParams& p = ctx->kp;
+    c3.clear();
+    uint32_t* base3 = const_cast<uint32_t*>(p.c3map[0]);
+    for (int k = 0; k < p.n3; ++k) {
+        p.c3map[k] = base3 + c3.size();
+        const int G = sweep3d_groups(p.L3[k], gm);
+        uint32_t n = 0;
+        for (int m = 0; m < (int)ctx->runs.size(); ++m) {
+            RunHost& h = ctx->runs[m];
+            if (h.L != p.L3[k]) continue;
+            h.nct3 = (h.ngrp + G - 1) / G;
+            ctx->desc[m].cta0 = n;
+            for (int c = 0; c < h.nct3; ++c) c3.push_back((uint32_t)m);
+            n += (uint32_t)h.nct3;
+        }
+        p.n3cta[k] = n;
+    }
+    p.g3mul = gm;
+}
+
 // all kernels of one temperature step (and the controller's choice of the next)
 pa_status enqueue_step(pa_ctx* ctx, int64_t* launches) {
     PA_CUDA(launch_resample(ctx->kp, ctx->stream, launches));
@@ -579,6 +603,8 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
     p.alpha = -1.0;
     p.qcap_limit = -1;
     p.lb_hold = 0;
+    p.n3 = 0;
+    p.g3mul = 1;
     p.L_all = ctx->runs[0].L;
     for (const RunHost& h : ctx->runs)
         if (h.L != p.L_all) p.L_all = 0;
@@ -668,20 +694,10 @@ pa_status pa_batch_init(pa_ctx** out, const pa_run_spec* specs, int32_t M,
             if (std::find(Ls.begin(), Ls.end(), h.L) == Ls.end()) Ls.push_back(h.L);
         }
         if (ok && Ls.size() <= 4) {
-            uint32_t* base3 = (uint32_t*)(base + lay.shared_off[S_C3]);
             p.n3 = (int)Ls.size();
-            for (int k = 0; k < p.n3; ++k) {
-                p.L3[k] = Ls[k];
-                p.c3map[k] = base3 + c3.size();
-                uint32_t n = 0;
-                for (int m = 0; m < M; ++m) {
-                    if (ctx->runs[m].L != Ls[k]) continue;
-                    ctx->desc[m].cta0 = n;
-                    for (int c = 0; c < ctx->runs[m].nct3; ++c) c3.push_back((uint32_t)m);
-                    n += (uint32_t)ctx->runs[m].nct3;
-                }
-                p.n3cta[k] = n;
-            }
+            for (int k = 0; k < p.n3; ++k) p.L3[k] = Ls[k];
+            p.c3map[0] = (uint32_t*)(base + lay.shared_off[S_C3]);
+            plan3d(ctx, 1, c3);
         }
     }
 
@@ -1241,7 +1257,34 @@ int64_t pa_launch_count(const pa_ctx* ctx) { return ctx ? ctx->launches : 0; }
 pa_status pa_set_sweep_threads(pa_ctx* ctx, int32_t threads) {
     if (!ctx || !sweep_threads_supported(threads)) return PA_ERR_ARG;
     ctx->threads = threads;
+    if (ctx->graph) {  // the captured step holds the old launch configuration
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
     return PA_OK;
+}
+
+pa_status pa_set_sweep_groups(pa_ctx* ctx, int32_t mult) {
+    if (!ctx || (mult != 1 && mult != 2)) return PA_ERR_ARG;
+    if (ctx->kp.n3 == 0) return mult == 1 ? PA_OK : PA_ERR_ARG;  // no grouped 3D kernel
+    if (ctx->sticky != PA_OK) return PA_ERR_STATE;
+    if (mult == ctx->kp.g3mul) return PA_OK;
+    // no step in flight may read the old plan
+    PA_CUDA(cudaStreamSynchronize(ctx->stream));
+    std::vector<uint32_t> c3;
+    plan3d(ctx, mult, c3);
+    PA_CUDA(cudaMemcpy((void*)ctx->kp.c3map[0], c3.data(), c3.size() * 4, cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy((void*)ctx->kp.runs, ctx->desc.data(), sizeof(RunDesc) * ctx->desc.size(),
+                       cudaMemcpyHostToDevice));
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return PA_OK;
+}
+
+int32_t pa_get_sweep_groups(const pa_ctx* ctx) {
+    return ctx ? (ctx->kp.n3 ? ctx->kp.g3mul : 1) : 0;
 }
 
 int32_t pa_get_sweep_threads(const pa_ctx* ctx) { return ctx ? ctx->threads : 0; }

@@ -222,6 +222,7 @@ struct KParams {
     // 3D kernel plan: one launch per distinct side (n3 = 0: the general kernel)
     int n3;
     int L3[4];
+    int g3mul;               // groups per CTA: the side's base count times this (1 or 2)
     const uint32_t* c3map[4];  // CTA -> run of each launch
     uint32_t n3cta[4];
 };
@@ -247,7 +248,7 @@ cudaError_t launch_family_finish(const KParams& p, int mode, cudaStream_t s, int
 cudaError_t prepare_sweep(const KParams& p, int threads);
 cudaError_t launch_sweep2d(const KParams& p, int threads, cudaStream_t s, bool attr_only,
                            bool* done);
-int sweep3d_groups(int L);
+int sweep3d_groups(int L, int gm);
 cudaError_t launch_sweep3d(const KParams& p, int L, const uint32_t* cta2run, uint32_t ncta,
                            cudaStream_t s, bool attr_only);
 cudaError_t launch_control(const KParams& p, cudaStream_t s);

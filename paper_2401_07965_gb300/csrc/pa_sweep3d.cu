@@ -43,10 +43,11 @@ struct Groups3 {
     static constexpr int value = L == 4 ? 16 : (L == 6 ? 8 : (L == 8 ? 4 : (L == 10 ? 2 : 1)));
 };
 
-template <int L>
+// GM: a multiple of the base group count (the autotuner may double it)
+template <int L, int GM = 1>
 struct Shape3 {
     static constexpr int P = L + 2, P2 = P * P, N = L * L * L, H = N / 2;
-    static constexpr int G = Groups3<L>::value;
+    static constexpr int G = Groups3<L>::value * GM;
     static constexpr int ITERS = (G * H + NT3 - 1) / NT3;
     static constexpr int W = (N + 31) / 32, WP = (W + 3) & ~3;
     static constexpr int CELLS = P * P * P;
@@ -258,9 +259,9 @@ __device__ __forceinline__ uint2 bond_entry(const uint8_t* jbits, int s) {
     return make_uint2(bx, by);
 }
 
-template <int L, bool EA>
+template <int L, bool EA, int GM>
 __global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* cta2run) {
-    using S = Shape3<L>;
+    using S = Shape3<L, GM>;
     constexpr int G = S::G, H = S::H, N = S::N, P = S::P, P2 = S::P2, NW = NT3 / 32;
     constexpr int W = S::W, WP = S::WP;
     extern __shared__ __align__(16) uint32_t smem[];
@@ -554,66 +555,73 @@ __global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* c
     if (threadIdx.x == 0 && sAcc) atomicAdd(&r.trace[i].accepts, sAcc);
 }
 
-template <int L, bool EA>
+template <int L, bool EA, int GM>
 size_t smem3d() {
-    using S = Shape3<L>;
+    using S = Shape3<L, GM>;
     return (size_t)S::LAT_WORDS * 4 + (size_t)2 * S::H * 8 * (EA ? 2 : 1) +
            (size_t)(NT3 / 32) * (S::QW + 32) * 16;
 }
 
-template <int L, bool EA>
+template <int L, bool EA, int GM>
 cudaError_t launch3d(const KParams& p, const uint32_t* cta2run, uint32_t ncta, cudaStream_t s,
                      bool attr_only) {
     static bool attr_set = false;
-    const size_t sm = smem3d<L, EA>();
+    const size_t sm = smem3d<L, EA, GM>();
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep3d<L, EA>,
+        cudaError_t e = cudaFuncSetAttribute(k_sweep3d<L, EA, GM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (attr_only || ncta == 0) return cudaSuccess;
-    k_sweep3d<L, EA><<<ncta, NT3, sm, s>>>(p, cta2run);
+    k_sweep3d<L, EA, GM><<<ncta, NT3, sm, s>>>(p, cta2run);
     return cudaGetLastError();
 }
 
-template <bool EA>
+template <bool EA, int GM>
 cudaError_t launch3d_L(int L, const KParams& p, const uint32_t* cta2run, uint32_t ncta,
                        cudaStream_t s, bool attr_only) {
     switch (L) {
-        case 4: return launch3d<4, EA>(p, cta2run, ncta, s, attr_only);
-        case 6: return launch3d<6, EA>(p, cta2run, ncta, s, attr_only);
-        case 8: return launch3d<8, EA>(p, cta2run, ncta, s, attr_only);
-        case 10: return launch3d<10, EA>(p, cta2run, ncta, s, attr_only);
-        case 12: return launch3d<12, EA>(p, cta2run, ncta, s, attr_only);
-        case 14: return launch3d<14, EA>(p, cta2run, ncta, s, attr_only);
-        default: return launch3d<16, EA>(p, cta2run, ncta, s, attr_only);
+        case 4: return launch3d<4, EA, GM>(p, cta2run, ncta, s, attr_only);
+        case 6: return launch3d<6, EA, GM>(p, cta2run, ncta, s, attr_only);
+        case 8: return launch3d<8, EA, GM>(p, cta2run, ncta, s, attr_only);
+        case 10: return launch3d<10, EA, GM>(p, cta2run, ncta, s, attr_only);
+        case 12: return launch3d<12, EA, GM>(p, cta2run, ncta, s, attr_only);
+        case 14: return launch3d<14, EA, GM>(p, cta2run, ncta, s, attr_only);
+        default: return launch3d<16, EA, GM>(p, cta2run, ncta, s, attr_only);
+    }
+}
+
+template <int GM>
+int groups_L(int L) {
+    switch (L) {
+        case 4: return Shape3<4, GM>::G;
+        case 6: return Shape3<6, GM>::G;
+        case 8: return Shape3<8, GM>::G;
+        case 10: return Shape3<10, GM>::G;
+        case 12: return Shape3<12, GM>::G;
+        case 14: return Shape3<14, GM>::G;
+        case 16: return Shape3<16, GM>::G;
+        default: return 0;
     }
 }
 
 }  // namespace
 
-// replica groups per CTA of the 3D kernel for side L (0: no 3D kernel for L)
-int sweep3d_groups(int L) {
-    switch (L) {
-        case 4: return Shape3<4>::G;
-        case 6: return Shape3<6>::G;
-        case 8: return Shape3<8>::G;
-        case 10: return Shape3<10>::G;
-        case 12: return Shape3<12>::G;
-        case 14: return Shape3<14>::G;
-        case 16: return Shape3<16>::G;
-        default: return 0;
-    }
-}
+// replica groups per CTA of the 3D kernel for side L with group multiple gm (1 or 2;
+// 0: no 3D kernel for L)
+int sweep3d_groups(int L, int gm) { return gm == 2 ? groups_L<2>(L) : groups_L<1>(L); }
 
 // One launch of the 3D kernel over the CTAs of the runs of side L (cta2run: their
-// run indices, device memory).  attr_only: function attributes only (before a
-// stream capture).
+// run indices, device memory), with the context's group multiple.  attr_only:
+// function attributes only (before a stream capture).
 cudaError_t launch_sweep3d(const KParams& p, int L, const uint32_t* cta2run, uint32_t ncta,
                            cudaStream_t s, bool attr_only) {
-    return p.ea ? launch3d_L<true>(L, p, cta2run, ncta, s, attr_only)
-                : launch3d_L<false>(L, p, cta2run, ncta, s, attr_only);
+    if (p.g3mul == 2)
+        return p.ea ? launch3d_L<true, 2>(L, p, cta2run, ncta, s, attr_only)
+                    : launch3d_L<false, 2>(L, p, cta2run, ncta, s, attr_only);
+    return p.ea ? launch3d_L<true, 1>(L, p, cta2run, ncta, s, attr_only)
+                : launch3d_L<false, 1>(L, p, cta2run, ncta, s, attr_only);
 }
 
 }  // namespace pa

@@ -36,7 +36,8 @@ EXPORTS = ["pa_workspace_bytes", "pa_init", "pa_step", "pa_sync", "pa_observable
            "pa_set_graph", "pa_set_controller", "pa_schedule_taken", "pa_mlp_scratch_bytes",
            "pa_mlp_forward", "pa_mlp_gradients", "pa_mlp_adam", "pa_overlap",
            "pa_set_partial_resampling", "pa_weighted_rows", "pa_set_sweep_queue",
-           "pa_run_schedule_taken", "pa_set_wait_test"]
+           "pa_run_schedule_taken", "pa_set_wait_test", "pa_set_sweep_groups",
+           "pa_get_sweep_groups"]
 
 
 class pa_lattice(C.Structure):
@@ -174,6 +175,9 @@ def _load():
     lib.pa_set_sweep_threads.argtypes = [vp, C.c_int32]
     lib.pa_set_sweep_queue.argtypes = [vp, C.c_int32]
     lib.pa_set_wait_test.argtypes = [vp, C.c_int32]
+    lib.pa_set_sweep_groups.argtypes = [vp, C.c_int32]
+    lib.pa_get_sweep_groups.argtypes = [vp]
+    lib.pa_get_sweep_groups.restype = C.c_int32
     lib.pa_get_sweep_threads.argtypes = [vp]
     lib.pa_get_sweep_threads.restype = C.c_int32
     lib.pa_strerror.argtypes = [C.c_int]
@@ -337,6 +341,14 @@ def pa_set_sweep_queue(ctx, cap):
 
 def pa_set_wait_test(ctx, on):
     _check(_lib.pa_set_wait_test(ctx, int(on)), "pa_set_wait_test")
+
+
+def pa_set_sweep_groups(ctx, mult):
+    _check(_lib.pa_set_sweep_groups(ctx, int(mult)), "pa_set_sweep_groups")
+
+
+def pa_get_sweep_groups(ctx) -> int:
+    return int(_lib.pa_get_sweep_groups(ctx))
 
 
 def pa_get_sweep_threads(ctx) -> int:
@@ -536,9 +548,12 @@ class Population:
                            seed, stream_ptr, ws_ptr, ws_bytes)
         if sweep_threads == "auto":  # the autotuner's choice for this shape (cached)
             from . import tune
-            sweep_threads = tune.best_sweep_threads_batch(
-                self._tune_specs(), theta=int(np.median(self.thetas)) if len(self.thetas) else 0,
-                stream=getattr(self, "_stream_obj", None))
+            th = int(np.median(self.thetas)) if len(self.thetas) else 0
+            specs, so = self._tune_specs(), getattr(self, "_stream_obj", None)
+            sweep_threads = tune.best_sweep_threads_batch(specs, theta=th, stream=so)
+            groups = tune.best_sweep_groups_batch(specs, theta=th, stream=so)
+            if groups > 1:
+                pa_set_sweep_groups(self.ctx, groups)
         if sweep_threads:
             pa_set_sweep_threads(self.ctx, sweep_threads)
 
@@ -647,9 +662,12 @@ class Batch:
                                  stream_ptr, ws_ptr, ws_bytes)
         if sweep_threads == "auto":  # the autotuner's choice for this shape (cached)
             from . import tune
-            sweep_threads = tune.best_sweep_threads_batch(
-                self._tune_specs(), theta=int(np.median(self.thetas)) if len(self.thetas) else 0,
-                stream=getattr(self, "_stream_obj", None))
+            th = int(np.median(self.thetas)) if len(self.thetas) else 0
+            specs, so = self._tune_specs(), getattr(self, "_stream_obj", None)
+            sweep_threads = tune.best_sweep_threads_batch(specs, theta=th, stream=so)
+            groups = tune.best_sweep_groups_batch(specs, theta=th, stream=so)
+            if groups > 1:
+                pa_set_sweep_groups(self.ctx, groups)
         if sweep_threads:
             pa_set_sweep_threads(self.ctx, sweep_threads)
         pa_set_graph(self.ctx, graph)

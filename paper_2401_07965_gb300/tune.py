@@ -3,7 +3,9 @@
 The sweep kernel runs one CTA per 32 replicas; how many threads share a CTA
 (64-512) trades per-CTA parallelism against the number of CTAs resident per
 SM and the rounding of the grid into waves, which depends on the lattice and
-on the population size.  The tuner times each candidate on a throw-away run of
+on the population size.  The grouped 3D kernel has a fixed CTA size and holds
+several replica groups per CTA; the tuner picks between that count and twice
+it.  The tuner times each candidate on a throw-away run of
 the same shape (same lattice, couplings kind, R and theta; results never
 depend on the choice) and remembers the fastest per device and shape, in
 memory and in a small JSON cache file.
@@ -102,6 +104,45 @@ def best_sweep_threads_batch(specs, theta=10, candidates=CANDIDATES, rounds=2, u
             best[t] = max(best.get(t, 0.0), rate)
     run.close()
     choice = max(best, key=best.get)
+    _CACHE[key] = int(choice)
+    if use_cache:
+        _save()
+    return int(choice)
+
+
+def best_sweep_groups_batch(specs, theta=10, rounds=2, use_cache=True, stream=None):
+    """Group multiple (1 or 2) of the fastest grouped 3D sweep for a batch of runs: 1 when
+    the runs do not use the grouped kernel, else both are timed on a throw-away batch of
+    the same runs (results never depend on the choice) and the faster is remembered."""
+    if any(s["dim"] != 3 for s in specs):
+        return 1
+    key = _batch_key(specs, theta) + "|groups"
+    if use_cache:
+        _load()
+        if key in _CACHE:
+            return int(_CACHE[key])
+    n = 2 * rounds + 1
+    betas = np.linspace(0.0, 0.5, n + 1)
+    thetas = np.full(n, theta, np.uint32)
+    run = pa.Batch([dict(s) for s in specs], betas, thetas, "systematic", 12345, stream=stream,
+                   graph=False)
+    choice = 1
+    try:
+        pa.pa_set_sweep_groups(run.ctx, 2)
+    except pa.PAError:
+        run.close()  # the runs take the general kernel
+    else:
+        run.step(1)  # first launch of each kernel outside the timings
+        best = {}
+        pa.pa_enable_timing(run.ctx, True)
+        for _ in range(rounds):
+            for g in (1, 2):
+                pa.pa_set_sweep_groups(run.ctx, g)
+                run.step(1)
+                ms, cnt, upd = pa.pa_sweep_timing(run.ctx)
+                best[g] = max(best.get(g, 0.0), upd / max(ms, 1e-9))
+        run.close()
+        choice = max(best, key=best.get)
     _CACHE[key] = int(choice)
     if use_cache:
         _save()

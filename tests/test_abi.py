@@ -123,3 +123,9 @@ def test_wait_test_hook_validates_arguments(lib):
     from paper_2401_07965_gb300 import pa
     assert pa._lib.pa_set_wait_test(None, 0) == pa.PA_ERR_ARG
     assert pa._lib.pa_set_wait_test(None, 1) == pa.PA_ERR_ARG
+
+
+def test_sweep_groups_hook_validates_arguments(lib):
+    from paper_2401_07965_gb300 import pa
+    assert pa._lib.pa_set_sweep_groups(None, 1) == pa.PA_ERR_ARG
+    assert pa._lib.pa_get_sweep_groups(None) == 0

@@ -236,6 +236,40 @@ def test_sweep_launch_configuration_does_not_change_results(d, L, kind):
         g = pa.Population(d, L, 10, betas, th, "nearest", 6, couplings=cpl, sweep_threads=96)
 
 
+def test_3d_group_multiple_does_not_change_results():
+    """The grouped 3D kernel with its base replica groups per CTA and with twice as many
+    (set before the first step, and changed between steps of a running batch): the
+    same spins, families and sums.  Contexts without the grouped kernel refuse 2."""
+    runs = [{"dim": 3, "L": 4, "R": 333, "couplings": ("ea", 3, 0)},
+            {"dim": 3, "L": 6, "R": 150, "couplings": ("ea", 3, 1)},
+            {"dim": 3, "L": 8, "R": 100, "couplings": ("ea", 3, 2)},
+            {"dim": 3, "L": 10, "R": 70, "couplings": ("ea", 3, 3)}]
+    betas = np.linspace(0, 2.0, 7)
+    th = np.full(6, 2, np.uint32)
+    out = []
+    for mode in ("one", "two", "switch"):
+        b = pa.Batch(runs, betas, th, "systematic", 8)
+        if mode == "two":
+            pa.pa_set_sweep_groups(b.ctx, 2)
+            assert pa.pa_get_sweep_groups(b.ctx) == 2
+        for k in range(6):
+            if mode == "switch":
+                pa.pa_set_sweep_groups(b.ctx, 2 if k % 2 else 1)
+            b.step(1)
+        out.append([(b.spins_words(m), b.array(m, pa.PA_ARRAY_FAMILY), b.observables(m))
+                    for m in range(len(runs))])
+        b.close()
+    for cur in out[1:]:
+        for (s0, f0, o0), (s1, f1, o1) in zip(out[0], cur):
+            assert np.array_equal(s0, s1) and np.array_equal(f0, f1) and o0 == o1
+    g = pa.Population(2, 16, 64, betas, th, "systematic", 3)
+    assert pa.pa_get_sweep_groups(g.ctx) == 1
+    pa.pa_set_sweep_groups(g.ctx, 1)
+    with pytest.raises(pa.PAError):
+        pa.pa_set_sweep_groups(g.ctx, 2)
+    g.close()
+
+
 @pytest.mark.parametrize("d,L,R,kind,method,bf,caps", [
     (2, 64, 96, "ferro", "systematic", 1.0, (0, 32)),
     (3, 6, 150, "ea", "poisson", 3.0, (0, 4)),
