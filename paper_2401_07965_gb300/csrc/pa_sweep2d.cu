@@ -490,27 +490,37 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
 }
 
 template <int L, int NT, bool EA>
-size_t smem2d() {
+constexpr size_t smem2d() {
     constexpr int P = L + 2, ITERS = L / (NT / (L / 2));
     constexpr int LAT_WORDS = (P * P + 3) & ~3;
     constexpr int QW = (32 * ITERS) / 4 + 32;
     return (size_t)LAT_WORDS * 4 + (EA ? (size_t)P * P * 16 : 0) + (size_t)(NT / 32) * (QW + 32) * 16;
 }
 
+// dynamic shared memory a CTA may take (the opt-in limit less the kernel's static part)
+constexpr size_t SMEM2D_MAX = 227 * 1024 - 2048;
+
+// *done = false for a shape whose lattice does not fit one CTA's shared memory (the
+// +-J bond records of L = 128): the general kernel takes those runs
 template <int L, int NT, bool EA>
-cudaError_t launch2d(const KParams& p, cudaStream_t s, bool attr_only) {
-    static bool attr_set = false;
-    const size_t sm = smem2d<L, NT, EA>();
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep2d<L, NT, EA>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sm);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+cudaError_t launch2d(const KParams& p, cudaStream_t s, bool attr_only, bool* done) {
+    constexpr size_t sm = smem2d<L, NT, EA>();
+    if constexpr (sm > SMEM2D_MAX) {
+        *done = false;
+        return cudaSuccess;
+    } else {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(k_sweep2d<L, NT, EA>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sm);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        if (attr_only) return cudaSuccess;
+        k_sweep2d<L, NT, EA><<<p.ngrp_total, NT, sm, s>>>(p);
+        return cudaGetLastError();
     }
-    if (attr_only) return cudaSuccess;
-    k_sweep2d<L, NT, EA><<<p.ngrp_total, NT, sm, s>>>(p);
-    return cudaGetLastError();
 }
 
 template <bool EA>
@@ -518,17 +528,17 @@ cudaError_t launch2d_shape(const KParams& p, int threads, cudaStream_t s, bool a
                            bool* done) {
     *done = true;
     switch (p.L_all * 1000 + threads) {
-        case 16064: return launch2d<16, 64, EA>(p, s, attr_only);
-        case 16128: return launch2d<16, 128, EA>(p, s, attr_only);
-        case 32128: return launch2d<32, 128, EA>(p, s, attr_only);
-        case 32256: return launch2d<32, 256, EA>(p, s, attr_only);
-        case 32512: return launch2d<32, 512, EA>(p, s, attr_only);
-        case 64128: return launch2d<64, 128, EA>(p, s, attr_only);
-        case 64256: return launch2d<64, 256, EA>(p, s, attr_only);
-        case 64512: return launch2d<64, 512, EA>(p, s, attr_only);
-        case 128128: return launch2d<128, 128, EA>(p, s, attr_only);
-        case 128256: return launch2d<128, 256, EA>(p, s, attr_only);
-        case 128512: return launch2d<128, 512, EA>(p, s, attr_only);
+        case 16064: return launch2d<16, 64, EA>(p, s, attr_only, done);
+        case 16128: return launch2d<16, 128, EA>(p, s, attr_only, done);
+        case 32128: return launch2d<32, 128, EA>(p, s, attr_only, done);
+        case 32256: return launch2d<32, 256, EA>(p, s, attr_only, done);
+        case 32512: return launch2d<32, 512, EA>(p, s, attr_only, done);
+        case 64128: return launch2d<64, 128, EA>(p, s, attr_only, done);
+        case 64256: return launch2d<64, 256, EA>(p, s, attr_only, done);
+        case 64512: return launch2d<64, 512, EA>(p, s, attr_only, done);
+        case 128128: return launch2d<128, 128, EA>(p, s, attr_only, done);
+        case 128256: return launch2d<128, 256, EA>(p, s, attr_only, done);
+        case 128512: return launch2d<128, 512, EA>(p, s, attr_only, done);
         default: *done = false; return cudaSuccess;
     }
 }

@@ -114,7 +114,10 @@ def test_3d_spin_glass_ragged(method):
                                         (2, 2, 40, "ferro"), (3, 2, 33, "ea"),
                                         (2, 32, 96, "ferro"), (2, 4, 1, "ferro"),
                                         (3, 8, 300, "ea"), (3, 12, 45, "ferro"),
-                                        (3, 14, 40, "ea"), (3, 16, 70, "ea")])
+                                        (3, 14, 40, "ea"), (3, 16, 70, "ea"),
+                                        (2, 16, 70, "ea"), (2, 32, 50, "ea"),
+                                        (2, 64, 40, "ea"), (2, 128, 40, "ferro"),
+                                        (2, 128, 33, "ea")])
 def test_lattice_shapes(d, L, R, kind):
     # a single replica under Poisson resampling dies out with probability 1/e per step
     for method in (("systematic", "poisson") if R > 8 else ("systematic", "nearest")):
@@ -215,7 +218,8 @@ def test_checkpoint_restore_continues_bit_for_bit():
         b.close()
 
 
-@pytest.mark.parametrize("d,L,kind", [(2, 64, "ferro"), (3, 6, "ea")])
+@pytest.mark.parametrize("d,L,kind", [(2, 64, "ferro"), (3, 6, "ea"), (2, 32, "ea"),
+                                      (2, 128, "ferro"), (2, 16, "ea")])
 def test_sweep_launch_configuration_does_not_change_results(d, L, kind):
     cpl, J = _couplings(d, L, kind)
     betas = np.linspace(0, 1.0, 5)
