@@ -240,14 +240,14 @@ def test_sweep_launch_configuration_does_not_change_results(d, L, kind):
         g = pa.Population(d, L, 10, betas, th, "nearest", 6, couplings=cpl, sweep_threads=96)
 
 
-def test_3d_group_multiple_does_not_change_results():
+@pytest.mark.parametrize("sides", [(4, 6, 8, 10), (12, 14, 16)])
+def test_3d_group_multiple_does_not_change_results(sides):
     """The grouped 3D kernel with its base replica groups per CTA and with twice as many
     (set before the first step, and changed between steps of a running batch): the
     same spins, families and sums.  Contexts without the grouped kernel refuse 2."""
-    runs = [{"dim": 3, "L": 4, "R": 333, "couplings": ("ea", 3, 0)},
-            {"dim": 3, "L": 6, "R": 150, "couplings": ("ea", 3, 1)},
-            {"dim": 3, "L": 8, "R": 100, "couplings": ("ea", 3, 2)},
-            {"dim": 3, "L": 10, "R": 70, "couplings": ("ea", 3, 3)}]
+    Rs = (333, 150, 100, 70)
+    runs = [{"dim": 3, "L": L, "R": Rs[k], "couplings": ("ea", 3, k)}
+            for k, L in enumerate(sides)]
     betas = np.linspace(0, 2.0, 7)
     th = np.full(6, 2, np.uint32)
     out = []
