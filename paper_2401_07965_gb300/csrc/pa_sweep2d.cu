@@ -135,6 +135,29 @@ __device__ __forceinline__ void classes(uint32_t P0, uint32_t P1, uint32_t P2, u
     c4 = need & any;
 }
 
+// three-input logic operation given by its truth table LUT = f(0xF0, 0xCC, 0xAA)
+template <int LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+}
+
+// the classes of a ferromagnet site from its word and its four neighbours (the same
+// values as classes() on P_k = w ^ n_k): each pair term takes the XORs with w inside
+// one three-input logic operation, which saves the four separate XORs
+__device__ __forceinline__ void classes_w(uint32_t w, uint32_t n0, uint32_t n1, uint32_t n2,
+                                          uint32_t n3, uint32_t vmask, uint32_t& need,
+                                          uint32_t& c4, uint32_t& c8) {
+    const uint32_t a = lop3<0x7E>(w, n0, n1), b = lop3<0x7E>(w, n2, n3);  // (w^x)|(w^y)
+    const uint32_t pa = lop3<0x18>(w, n0, n1), pb = lop3<0x18>(w, n2, n3);  // (w^x)&(w^y)
+    const uint32_t any = a | b;
+    const uint32_t two = pa | pb | (a & b);
+    need = ~two & vmask;
+    c8 = ~any;
+    c4 = need & any;
+}
+
 // the top eight planes at once (blocks 0 and 1): b = [u8 < t8] by the borrow of
 // u - t from the least significant plane up, eq = [u8 == t8], per replica with
 // t the threshold of its class
@@ -207,16 +230,18 @@ __device__ __forceinline__ void site_pass1(uint32_t* la, const uint4* ja, uint32
                                            uint32_t& acc) {
     constexpr int P = L + 2;
     const uint32_t w = la[0];
-    uint32_t P0 = w ^ la[1], P1 = w ^ la[-1], P2 = w ^ la[P], P3 = w ^ la[-P];
+    uint32_t need, c4, c8;
     if (EA) {
+        uint32_t P0 = w ^ la[1], P1 = w ^ la[-1], P2 = w ^ la[P], P3 = w ^ la[-P];
         const uint4 J = *ja;
         P0 ^= J.x;
         P1 ^= J.y;
         P2 ^= J.z;
         P3 ^= J.w;
+        classes(P0, P1, P2, P3, hs.vmask, need, c4, c8);
+    } else {
+        classes_w(w, la[1], la[-1], la[P], la[-P], hs.vmask, need, c4, c8);
     }
-    uint32_t need, c4, c8;
-    classes(P0, P1, P2, P3, hs.vmask, need, c4, c8);
     const uint32_t A2s = hs.A2s0 ^ s_hi;
     uint32_t B1, h0c, l0c;
     site_rounds(A2s, hs.B1k, B1, h0c, l0c);
@@ -252,16 +277,18 @@ __device__ __forceinline__ void site_pass2(uint32_t* lat, const uint4* jw, const
         const int c = Geo2<L>::cell((int)(s & (L - 1)), (int)(s >> LG));
         uint32_t* la = lat + c;
         const uint32_t w = la[0];
-        uint32_t P0 = w ^ la[1], P1 = w ^ la[-1], P2 = w ^ la[P], P3 = w ^ la[-P];
+        uint32_t need, c4, c8;
         if (EA) {
+            uint32_t P0 = w ^ la[1], P1 = w ^ la[-1], P2 = w ^ la[P], P3 = w ^ la[-P];
             const uint4 J = jw[c];
             P0 ^= J.x;
             P1 ^= J.y;
             P2 ^= J.z;
             P3 ^= J.w;
+            classes(P0, P1, P2, P3, vmask, need, c4, c8);
+        } else {
+            classes_w(w, la[1], la[-1], la[P], la[-P], vmask, need, c4, c8);
         }
-        uint32_t need, c4, c8;
-        classes(P0, P1, P2, P3, vmask, need, c4, c8);
         uint32_t B1, h0c, l0c;
         site_rounds(q.x, B1k, B1, h0c, l0c);
         finish(c4, c8, tab, B1, h0c, l0c, p, und, lt);
