@@ -135,14 +135,6 @@ __device__ __forceinline__ void classes(uint32_t P0, uint32_t P1, uint32_t P2, u
     c4 = need & any;
 }
 
-// three-input logic operation given by its truth table LUT = f(0xF0, 0xCC, 0xAA)
-template <int LUT>
-__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
-    uint32_t d;
-    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
-    return d;
-}
-
 // the classes of a ferromagnet site from its word and its four neighbours (the same
 // values as classes() on P_k = w ^ n_k): each pair term takes the XORs with w inside
 // one three-input logic operation, which saves the four separate XORs
@@ -169,14 +161,14 @@ __device__ __forceinline__ void cmp8(uint32_t c4, uint32_t c8, const Tab2& e, co
 #pragma unroll
     for (int m = 3; m >= 0; --m) {
         const uint32_t t = c4 * f.B0[m] + c8 * f.B1[m];
-        b = (~V[m] & t) | (~(V[m] ^ t) & b);
-        eq &= ~(V[m] ^ t);
+        b = lop3<0x8E>(V[m], t, b);    // (~V & t) | (~(V ^ t) & b)
+        eq = lop3<0x82>(V[m], t, eq);  // eq & ~(V ^ t)
     }
 #pragma unroll
     for (int m = 3; m >= 0; --m) {
         const uint32_t t = c4 * e.B0[m] + c8 * e.B1[m];
-        b = (~W[m] & t) | (~(W[m] ^ t) & b);
-        eq &= ~(W[m] ^ t);
+        b = lop3<0x8E>(W[m], t, b);
+        eq = lop3<0x82>(W[m], t, eq);
     }
 }
 
@@ -187,8 +179,8 @@ __device__ __forceinline__ void cmp4(uint32_t c4, uint32_t c8, const Tab2& e,
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const uint32_t t = c4 * e.B0[m] + c8 * e.B1[m];
-        lt |= und & t & ~W[m];
-        und &= ~(W[m] ^ t);
+        lt |= lop3<0x40>(und, t, W[m]);   // und & t & ~W
+        und = lop3<0x82>(W[m], t, und);   // und & ~(W ^ t)
     }
 }
 

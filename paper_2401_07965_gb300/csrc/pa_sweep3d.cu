@@ -118,19 +118,25 @@ __device__ __forceinline__ void draw1_3(const uint4 e, uint32_t B1, uint32_t h0c
     W[0] = x0; W[1] = x1; W[2] = x2; W[3] = x3;
 }
 
-// classes from the six bond planes (unsatisfied = 1): n unsatisfied bonds as a
-// bit-sliced count (n2 n1 n0); need = n <= 2 among the valid replicas
-__device__ __forceinline__ void classes3(uint32_t P0, uint32_t P1, uint32_t P2, uint32_t P3,
-                                         uint32_t P4, uint32_t P5, uint32_t vmask, uint32_t& need,
-                                         uint32_t& c4, uint32_t& c8, uint32_t& c12) {
-    const uint32_t sa = P0 ^ P1 ^ P2, ca = (P0 & P1) | (P2 & (P0 ^ P1));
-    const uint32_t sb = P3 ^ P4 ^ P5, cb = (P3 & P4) | (P5 & (P3 ^ P4));
-    const uint32_t n0 = sa ^ sb, kc = sa & sb;
-    const uint32_t n1 = ca ^ cb ^ kc, n2 = (ca & cb) | (kc & (ca ^ cb));
-    need = ~n2 & ~(n1 & n0) & vmask;
-    c12 = ~(n0 | n1 | n2);
-    c8 = ~n2 & ~n1 & n0;
-    c4 = ~n2 & n1 & ~n0;
+// classes from the site word w and its six bond partners a[i] (neighbour word,
+// XOR the bond's sign for the spin glass; bond i is unsatisfied where w ^ a[i] =
+// 1): n unsatisfied bonds as a bit-sliced count (n2 n1 n0); need = n <= 2 among
+// the valid replicas.  The sum and carry of a triple of bonds are
+// w ^ (a ^ b ^ c) and w ^ maj(a, b, c), so w cancels from n0 and n1 and enters
+// only the two carries of the second stage.
+__device__ __forceinline__ void classes3_w(uint32_t w, const uint32_t (&a)[6], uint32_t vmask,
+                                           uint32_t& need, uint32_t& c4, uint32_t& c8,
+                                           uint32_t& c12) {
+    const uint32_t x3 = lop3<0x96>(a[0], a[1], a[2]), ma = lop3<0xE8>(a[0], a[1], a[2]);
+    const uint32_t y3 = lop3<0x96>(a[3], a[4], a[5]), mb = lop3<0xE8>(a[3], a[4], a[5]);
+    const uint32_t n0 = x3 ^ y3;
+    const uint32_t kc = lop3<0x18>(w, x3, y3);                         // (w^x3)&(w^y3)
+    const uint32_t n1 = lop3<0x96>(ma, mb, kc);
+    const uint32_t n2 = lop3<0x18>(w, ma, mb) | lop3<0x60>(kc, ma, mb); // carry of the carries
+    need = lop3<0x07>(n2, n1, n0) & vmask;                             // ~n2 & ~(n1 & n0)
+    c12 = lop3<0x01>(n0, n1, n2);
+    c8 = lop3<0x10>(n0, n1, n2);
+    c4 = lop3<0x04>(n0, n1, n2);
 }
 
 // threshold bits of a plane block for the three classes (0 or 1 per plane)
@@ -157,15 +163,15 @@ __device__ __forceinline__ void cmp8_3(uint32_t c4, uint32_t c8, uint32_t c12, c
 #pragma unroll
     for (int m = 3; m >= 0; --m) {
         const uint32_t t = thr_word(c4, c8, c12, f, m);
-        b = (~V[m] & t) | (~(V[m] ^ t) & b);
-        eq &= ~(V[m] ^ t);
+        b = lop3<0x8E>(V[m], t, b);    // (~V & t) | (~(V ^ t) & b)
+        eq = lop3<0x82>(V[m], t, eq);  // eq & ~(V ^ t)
     }
     const BlockBits e = bt[0];
 #pragma unroll
     for (int m = 3; m >= 0; --m) {
         const uint32_t t = thr_word(c4, c8, c12, e, m);
-        b = (~W[m] & t) | (~(W[m] ^ t) & b);
-        eq &= ~(W[m] ^ t);
+        b = lop3<0x8E>(W[m], t, b);
+        eq = lop3<0x82>(W[m], t, eq);
     }
 }
 
@@ -182,8 +188,8 @@ __device__ __forceinline__ void finish3(uint32_t c4, uint32_t c8, uint32_t c12, 
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const uint32_t tm = thr_word(c4, c8, c12, t, m);
-            lt |= und & tm & ~W[m];
-            und &= ~(W[m] ^ tm);
+            lt |= lop3<0x40>(und, tm, W[m]);   // und & tm & ~W
+            und = lop3<0x82>(W[m], tm, und);   // und & ~(W ^ tm)
         }
     }
 }
@@ -199,23 +205,23 @@ __device__ __forceinline__ uint32_t sign_of_byte(uint32_t v) {
 
 // the six bond planes of a site: j holds its bond signs as byte sign bits, x
 // bytes 0-3 the bonds to +x, -x, +y, -y and y bytes 0-1 those to +z, -z
+// the six bond partners of a site: neighbour words, XOR the bond signs for EA
 template <int L, bool EA>
-__device__ __forceinline__ void bond_planes(const uint32_t* la, uint2 j, uint32_t w,
-                                            uint32_t (&P)[6]) {
+__device__ __forceinline__ void bond_partners(const uint32_t* la, uint2 j, uint32_t (&a)[6]) {
     constexpr int PP = L + 2, P2 = PP * PP;
-    P[0] = w ^ la[1];
-    P[1] = w ^ la[-1];
-    P[2] = w ^ la[PP];
-    P[3] = w ^ la[-PP];
-    P[4] = w ^ la[P2];
-    P[5] = w ^ la[-P2];
+    a[0] = la[1];
+    a[1] = la[-1];
+    a[2] = la[PP];
+    a[3] = la[-PP];
+    a[4] = la[P2];
+    a[5] = la[-P2];
     if (EA) {
-        P[0] ^= sign_of_byte<0x8888>(j.x);
-        P[1] ^= sign_of_byte<0x9999>(j.x);
-        P[2] ^= sign_of_byte<0xAAAA>(j.x);
-        P[3] ^= sign_of_byte<0xBBBB>(j.x);
-        P[4] ^= sign_of_byte<0x8888>(j.y);
-        P[5] ^= sign_of_byte<0x9999>(j.y);
+        a[0] ^= sign_of_byte<0x8888>(j.x);
+        a[1] ^= sign_of_byte<0x9999>(j.x);
+        a[2] ^= sign_of_byte<0xAAAA>(j.x);
+        a[3] ^= sign_of_byte<0xBBBB>(j.x);
+        a[4] ^= sign_of_byte<0x8888>(j.y);
+        a[5] ^= sign_of_byte<0x9999>(j.y);
     }
 }
 
@@ -244,7 +250,7 @@ __device__ __forceinline__ uint2 site_entry(int s) {
     return make_uint2((uint32_t)S::cell(x, y, z) | (faces << 16), (uint32_t)s);
 }
 
-// the bond-sign word of site s (layout of bond_planes) from the coupling bits
+// the bond-sign word of site s (layout of bond_partners) from the coupling bits
 // (bit a of jbits[s]: bond (s, s + e_a) has J = -1)
 template <int L>
 __device__ __forceinline__ uint2 bond_entry(const uint8_t* jbits, int s) {
@@ -411,10 +417,10 @@ __global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* c
                 const uint32_t s = en.y;
                 const uint32_t vm = have ? sVm[g] : 0u;
                 const uint32_t w = la[0];
-                uint32_t Pb[6];
-                bond_planes<L, EA>(la, EA ? cj[q] : make_uint2(0u, 0u), w, Pb);
+                uint32_t ab[6];
+                bond_partners<L, EA>(la, EA ? cj[q] : make_uint2(0u, 0u), ab);
                 uint32_t need, c4, c8, c12;
-                classes3(Pb[0], Pb[1], Pb[2], Pb[3], Pb[4], Pb[5], vm, need, c4, c8, c12);
+                classes3_w(w, ab, vm, need, c4, c8, c12);
                 const uint32_t A2s = sA2x[g] ^ s;
                 uint32_t B1, h0c, l0c;
                 {
@@ -447,10 +453,10 @@ __global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* c
                 uint32_t* la = lat + g * S::CELLS + (en.x & 0xFFFFu);
                 const uint32_t vm = sVm[g];
                 const uint32_t w = la[0];
-                uint32_t Pb[6];
-                bond_planes<L, EA>(la, EA ? cj[q] : make_uint2(0u, 0u), w, Pb);
+                uint32_t ab[6];
+                bond_partners<L, EA>(la, EA ? cj[q] : make_uint2(0u, 0u), ab);
                 uint32_t need, c4, c8, c12;
-                classes3(Pb[0], Pb[1], Pb[2], Pb[3], Pb[4], Pb[5], vm, need, c4, c8, c12);
+                classes3_w(w, ab, vm, need, c4, c8, c12);
                 uint32_t B1, h0c, l0c;
                 {
                     uint32_t h1b, l1b;

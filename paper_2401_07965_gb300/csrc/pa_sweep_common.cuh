@@ -7,6 +7,14 @@
 
 namespace pa {
 
+// three-input logic operation given by its truth table LUT = f(0xF0, 0xCC, 0xAA)
+template <int LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+}
+
 __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
     // lane i holds row i (bit c = element (i, c)); returns column `lane`
     const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
@@ -138,8 +146,8 @@ __device__ __forceinline__ void block_compare(SiteCmp<D>& c, const PlaneTab& e,
         uint32_t tm = c.cls[0] * e.B[m][0];
 #pragma unroll
         for (int a = 1; a < D; ++a) tm += c.cls[a] * e.B[m][a];
-        lt |= und & tm & ~W[m];  // u bit 0, thr bit 1: u < thr
-        und &= ~(W[m] ^ tm);     // equal bits: still undecided
+        lt |= lop3<0x40>(und, tm, W[m]);  // und & tm & ~W: u bit 0, thr bit 1: u < thr
+        und = lop3<0x82>(W[m], tm, und);  // und & ~(W ^ tm): equal bits, still undecided
     }
     c.und = und;
     c.lt = lt;
@@ -159,16 +167,16 @@ __device__ __forceinline__ void compare8(SiteCmp<D>& c, const PlaneTab& e, const
         uint32_t t = c.cls[0] * f.B[m][0];
 #pragma unroll
         for (int a = 1; a < D; ++a) t += c.cls[a] * f.B[m][a];
-        b = (~V[m] & t) | (~(V[m] ^ t) & b);
-        eq &= ~(V[m] ^ t);
+        b = lop3<0x8E>(V[m], t, b);    // (~V & t) | (~(V ^ t) & b)
+        eq = lop3<0x82>(V[m], t, eq);  // eq & ~(V ^ t)
     }
 #pragma unroll
     for (int m = 3; m >= 0; --m) {
         uint32_t t = c.cls[0] * e.B[m][0];
 #pragma unroll
         for (int a = 1; a < D; ++a) t += c.cls[a] * e.B[m][a];
-        b = (~W[m] & t) | (~(W[m] ^ t) & b);
-        eq &= ~(W[m] ^ t);
+        b = lop3<0x8E>(W[m], t, b);
+        eq = lop3<0x82>(W[m], t, eq);
     }
     c.lt = b & c.need;
     c.und = eq & c.need;
