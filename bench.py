@@ -61,26 +61,56 @@ WORKLOAD = ("2D Ising ferromagnet L=64 periodic, R=100000, beta 0->1 in 200 step
 # schedulers issue 4 warp instructions (128 lane-instructions).  The roofline is
 # set by the most loaded of the three.
 E_BLOCKS = sum(1.0 - (1.0 - 16.0 ** -g) ** 32 for g in range(8))
-ALU_OPS_PER_SITEWORD = 12 + E_BLOCKS * (17 + 4 * 2)
+# weights of plane blocks 0 and 1 in E_B; the kernels draw these two for every site
+HEAD_BLOCKS = 1.0 + (1.0 - (15.0 / 16.0) ** 32)
 MULWIDE_PER_SITEWORD = 2 + E_BLOCKS * 14
-IMAD_PER_SITEWORD = E_BLOCKS * 4 * 2
-FMA_CYCLES_PER_SITEWORD = 2 * MULWIDE_PER_SITEWORD + IMAD_PER_SITEWORD
-ISSUE_PER_SITEWORD = ALU_OPS_PER_SITEWORD + MULWIDE_PER_SITEWORD + IMAD_PER_SITEWORD
 ALU_LANES_PER_SM = 64
 FMA_LANES_PER_SM = 64
 ISSUE_LANES_PER_SM = 128
-PIPES = {"alu": (ALU_OPS_PER_SITEWORD, ALU_LANES_PER_SM),
-         "fma": (FMA_CYCLES_PER_SITEWORD, FMA_LANES_PER_SM),
-         "issue": (ISSUE_PER_SITEWORD, ISSUE_LANES_PER_SM)}
-BINDING_PIPE = max(PIPES, key=lambda k: PIPES[k][0] / PIPES[k][1])
-ALU_OPS_PER_UPDATE = ALU_OPS_PER_SITEWORD / 32.0
-# d = 3 (six bonds, classes dE = 4, 8, 12): per site 22 logic operations (six
-# neighbour XORs, the bit-sliced count of unsatisfied bonds, the class masks, the
-# flip) and per plane one multiply and two multiply-adds for the threshold word
-PIPES3 = {"alu": (22 + E_BLOCKS * (17 + 4 * 2), ALU_LANES_PER_SM),
-          "fma": (2 * MULWIDE_PER_SITEWORD + E_BLOCKS * 4 * 3, FMA_LANES_PER_SM),
-          "issue": (22 + E_BLOCKS * (17 + 4 * 2) + MULWIDE_PER_SITEWORD + E_BLOCKS * 4 * 3,
-                    ISSUE_LANES_PER_SM)}
+
+
+def zero_classes(d, beta):
+    """Energy classes (dE = 4k, from the highest down) whose threshold exp(-beta dE)
+    is below 2^-8, i.e. has eight zero top bits: their threshold terms vanish in plane
+    blocks 0 and 1, which the kernels then leave out."""
+    zc = 0
+    for k in range(2 if d == 2 else 3, 0, -1):
+        if math.exp(-4.0 * k * beta) >= 2.0 ** -8:
+            break
+        zc += 1
+    return zc
+
+
+def pipes_model(d, zc=0):
+    """Per-site-word demand on the three integer resources (see the comment above).
+    d = 3: six bonds, classes dE = 4, 8, 12: per site 22 logic operations (six
+    neighbour XORs, the bit-sliced count of unsatisfied bonds, the class masks, the
+    flip) and per plane one multiply and two multiply-adds for the threshold word.
+    zc classes with eight zero top threshold bits need no multiply-add in blocks 0
+    and 1; with none left (t = 0) the borrow is 0 and the equality word takes 4 logic
+    operations for the 8 planes."""
+    ncls = 2 if d == 2 else 3
+    nc = ncls - zc
+    tail = E_BLOCKS - HEAD_BLOCKS
+    cmp_logic = 4 * (2.0 if nc > 0 else 0.5) * HEAD_BLOCKS + 4 * 2 * tail
+    imad = 4 * nc * HEAD_BLOCKS + 4 * ncls * tail
+    alu = (12 if d == 2 else 22) + E_BLOCKS * 17 + cmp_logic
+    fma = 2 * MULWIDE_PER_SITEWORD + imad
+    issue = alu + MULWIDE_PER_SITEWORD + imad
+    return {"alu": (alu, ALU_LANES_PER_SM), "fma": (fma, FMA_LANES_PER_SM),
+            "issue": (issue, ISSUE_LANES_PER_SM)}
+
+
+def mean_pipes(d, betas):
+    """pipes_model averaged over timed steps at inverse temperatures `betas` (equal
+    work per step), and how many steps had each number of zero classes."""
+    models = [pipes_model(d, zero_classes(d, b)) for b in betas]
+    out = {k: (sum(m[k][0] for m in models) / len(models), models[0][k][1]) for k in models[0]}
+    hist = {}
+    for b in betas:
+        z = zero_classes(d, b)
+        hist[z] = hist.get(z, 0) + 1
+    return out, hist
 
 
 def roofline_record(pipes, rate, nsm, f_hz):
@@ -401,7 +431,10 @@ def run_ours(args):
     clocks = clk.summary()
     f_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     sweep_rate = sweep_upd / (sweep_ms * 1e6)  # updates / ns inside the sweep kernel
-    per_sw, lanes = PIPES[BINDING_PIPE]
+    # the model's demand averaged over the timed steps' temperatures
+    pipes_t, zc_hist = mean_pipes(DIM, [betas[i] for _, i in timed_steps])
+    binding = max(pipes_t, key=lambda k: pipes_t[k][0] / pipes_t[k][1])
+    per_sw, lanes = pipes_t[binding]
     peak = nsm * lanes * f_hz / 1e12                       # T lane-operations / s
     achieved = per_sw / 32.0 * sweep_rate * 1e9 / 1e12
     traffic_full = _sweep_traffic(_src_hash())
@@ -409,18 +442,21 @@ def run_ours(args):
             "frac": achieved / peak, "traffic": traffic_full,
             "kernel": "k_sweep2d<64,T,false> (gather + theta bit-plane Metropolis sweeps + "
                       "measure)",
-            "binding_pipe": BINDING_PIPE,
-            "peak_source": f"{nsm} SMs x {lanes} lanes of the {BINDING_PIPE} pipe x sm_max_mhz "
+            "binding_pipe": binding,
+            "peak_source": f"{nsm} SMs x {lanes} lanes of the {binding} pipe x sm_max_mhz "
                            f"({peak_src} clocks); lanes per pipe from ncu's pipe peaks",
-            "per_site_word": {k: v[0] for k, v in PIPES.items()},
+            "per_site_word": {k: v[0] for k, v in pipes_t.items()},
+            "zero_class_steps": {str(z): c for z, c in sorted(zc_hist.items())},
             "pipe_fracs": {k: v[0] / 32.0 * sweep_rate * 1e9 / (nsm * v[1] * f_hz)
-                           for k, v in PIPES.items()},
+                           for k, v in pipes_t.items()},
             "sweep_updates_per_ns": sweep_rate,
             "sweep_launches_timed": sweep_n,
             "roofline_updates_per_ns": peak * 1e3 * 32.0 / per_sw,
             "sweep_share_of_step_time": sweep_ms / total_ms if world == 1 else None}
     if ea3d and "sweep_updates_per_ns" in ea3d:
-        ea3d["roofline"] = roofline_record(PIPES3, ea3d["sweep_updates_per_ns"], nsm, f_hz)
+        p3, h3 = mean_pipes(3, ea3d["timed_betas"])
+        ea3d["roofline"] = roofline_record(p3, ea3d["sweep_updates_per_ns"], nsm, f_hz)
+        ea3d["roofline"]["zero_class_steps"] = {str(z): c for z, c in sorted(h3.items())}
         ea3d["roofline"]["kernel"] = "k_sweep3d<L,true> (L = 4, 6, 8; grouped replicas)"
     cpu = cpu_mt = None
     if not args.no_cpu_baseline and world == 1:
@@ -540,7 +576,8 @@ def ea3d_batch(pa, stream, realizations=64, steps=20, warmup=5, timed_sweeps=Fal
     R_check = [b.observables(m)["R_i"] for m in (0, realizations, 2 * realizations)]
     b.close()
     out = {"updates_per_ns": upd_step * len(timed) / (ms * 1e6), "ms_per_step": ms / len(timed),
-           "timed_steps": timed, "runs": len(runs), "R_i_check": R_check}
+           "timed_steps": timed, "timed_betas": [float(betas[t]) for t in timed],
+           "runs": len(runs), "R_i_check": R_check}
     if timed_sweeps:
         out["sweep_updates_per_ns"] = upd_step * len(timed) / (sweep_ms * 1e6)
         out["sweep_share_of_step_time"] = sweep_ms / ms

@@ -152,25 +152,44 @@ __device__ __forceinline__ void classes_w(uint32_t w, uint32_t n0, uint32_t n1, 
 
 // the top eight planes at once (blocks 0 and 1): b = [u8 < t8] by the borrow of
 // u - t from the least significant plane up, eq = [u8 == t8], per replica with
-// t the threshold of its class
+// t the threshold of its class.  ZC: the number of classes, from dE = 8 down,
+// whose thresholds have eight zero top bits in this step (their terms of t are
+// zero and left out); with both, t = 0: b = 0 and eq = [u8 == 0].
+template <int ZC>
 __device__ __forceinline__ void cmp8(uint32_t c4, uint32_t c8, const Tab2& e, const Tab2& f,
                                      const uint32_t (&W)[4], const uint32_t (&V)[4], uint32_t& b,
                                      uint32_t& eq) {
+    if constexpr (ZC >= 2) {
+        b = 0u;
+        eq = lop3<0x01>(lop3<0xFE>(V[0], V[1], V[2]), lop3<0xFE>(V[3], W[0], W[1]),
+                        W[2] | W[3]);  // ~(a | b | c)
+        return;
+    }
     b = 0u;
     eq = 0xFFFFFFFFu;
 #pragma unroll
     for (int m = 3; m >= 0; --m) {
-        const uint32_t t = c4 * f.B0[m] + c8 * f.B1[m];
+        const uint32_t t = ZC == 0 ? c4 * f.B0[m] + c8 * f.B1[m] : c4 * f.B0[m];
         b = lop3<0x8E>(V[m], t, b);    // (~V & t) | (~(V ^ t) & b)
         eq = lop3<0x82>(V[m], t, eq);  // eq & ~(V ^ t)
     }
 #pragma unroll
     for (int m = 3; m >= 0; --m) {
-        const uint32_t t = c4 * e.B0[m] + c8 * e.B1[m];
+        const uint32_t t = ZC == 0 ? c4 * e.B0[m] + c8 * e.B1[m] : c4 * e.B0[m];
         b = lop3<0x8E>(W[m], t, b);
         eq = lop3<0x82>(W[m], t, eq);
     }
 }
+
+// ZC of a step from its thresholds of dE = 4 and 8 (top eight bits)
+__device__ __forceinline__ int zero_classes2(uint32_t thr4, uint32_t thr8) {
+    return (thr8 >> 24) != 0u ? 0 : ((thr4 >> 24) != 0u ? 1 : 2);
+}
+
+template <int V>
+struct IC {
+    static constexpr int value = V;
+};
 
 // four more planes from the top: replicas leave at the first plane where u and
 // thr differ
@@ -215,7 +234,7 @@ struct Half {
 // an undecided one is queued as (round-1 lane 2 with the site, und, lt) at slot
 // wq + (its rank among the warp's undecided sites); the other lanes write their
 // scratch slot qscratch + lane.
-template <int L, bool EA>
+template <int L, bool EA, int ZC>
 __device__ __forceinline__ void site_pass1(uint32_t* la, const uint4* ja, uint32_t s_hi,
                                            const Half& hs, const KParams& p, uint4* queue,
                                            int qscratch, uint32_t lml, int lane, int& wq,
@@ -240,7 +259,7 @@ __device__ __forceinline__ void site_pass1(uint32_t* la, const uint4* ja, uint32
     uint32_t W[4], V[4];
     draw2(hs.tab[0], hs.tab[1], B1, h0c, l0c, p, W, V);
     uint32_t b, eq;
-    cmp8(c4, c8, hs.tab[0], hs.tab[1], W, V, b, eq);
+    cmp8<ZC>(c4, c8, hs.tab[0], hs.tab[1], W, V, b, eq);
     const uint32_t lt = b & need;
     const uint32_t und = eq & need;
     const bool undecided = und != 0u;
@@ -385,6 +404,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
         B1k = l1a ^ p.rk0[1];
     }
     const uint32_t nh = 2u * r.stheta[i - 1];
+    const int zc = zero_classes2(r.sthr[4 * (i - 1) + 1], r.sthr[4 * (i - 1) + 2]);
     if (nh > 0 && threadIdx.x < 8)
         build_tab2(tabs[0], threadIdx.x, p, grp, (uint32_t)i, 0u, 0, r.sthr[4 * (i - 1) + 1],
                    r.sthr[4 * (i - 1) + 2]);
@@ -422,10 +442,18 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
         int k = 0;
         while (true) {
             int wq = 0;
+            // one copy of the walk per ZC (the same for the whole launch)
+            auto pass1 = [&](auto zc_tag) {
+                constexpr int ZC = decltype(zc_tag)::value;
 #pragma unroll 1
-            for (; k < ITERS && wq <= qflush; ++k)
-                site_pass1<L, EA>(la0 + k * RP * P, ja0 + k * RP * P, (uint32_t)(k * RP * L), hs,
-                                  p, queue, QW, lml, lane, wq, acc);
+                for (; k < ITERS && wq <= qflush; ++k)
+                    site_pass1<L, EA, ZC>(la0 + k * RP * P, ja0 + k * RP * P,
+                                          (uint32_t)(k * RP * L), hs, p, queue, QW, lml, lane,
+                                          wq, acc);
+            };
+            if (zc == 0) pass1(IC<0>{});
+            else if (zc == 1) pass1(IC<1>{});
+            else pass1(IC<2>{});
             site_pass2<L, EA>(lat, jw, queue, wq, lane, A2x, B1k, vmask, hs.tab, p, acc);
             if (k == ITERS) break;
         }

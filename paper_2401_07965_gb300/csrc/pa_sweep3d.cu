@@ -153,23 +153,54 @@ __device__ __forceinline__ uint32_t thr_word(uint32_t c4, uint32_t c8, uint32_t 
     return c4 * lane4(t.b4, m) + c8 * lane4(t.b8, m) + c12 * lane4(t.b12, m);
 }
 
-// planes 0-7 by the borrow of the subtraction from the least significant plane up
+// the threshold word of plane m of a block with the terms of the ZC highest
+// classes (dE = 12, then 8, then 4) left out: their top eight bits are zero
+template <int ZC>
+__device__ __forceinline__ uint32_t thr_word_z(uint32_t c4, uint32_t c8, uint32_t c12,
+                                               const BlockBits& t, int m) {
+    if constexpr (ZC == 0) return thr_word(c4, c8, c12, t, m);
+    if constexpr (ZC == 1) return c4 * lane4(t.b4, m) + c8 * lane4(t.b8, m);
+    return c4 * lane4(t.b4, m);
+}
+
+// ZC of a step from its thresholds of dE = 4, 8 and 12 (top eight bits)
+__device__ __forceinline__ int zero_classes3(uint32_t thr4, uint32_t thr8, uint32_t thr12) {
+    if ((thr12 >> 24) != 0u) return 0;
+    if ((thr8 >> 24) != 0u) return 1;
+    return (thr4 >> 24) != 0u ? 2 : 3;
+}
+
+template <int V>
+struct IC {
+    static constexpr int value = V;
+};
+
+// planes 0-7 by the borrow of the subtraction from the least significant plane
+// up; with ZC = 3 (every threshold's top eight bits zero) t = 0: b = 0 and
+// eq = [u8 == 0]
+template <int ZC>
 __device__ __forceinline__ void cmp8_3(uint32_t c4, uint32_t c8, uint32_t c12, const BlockBits* bt,
                                        const uint32_t (&W)[4], const uint32_t (&V)[4],
                                        uint32_t& b, uint32_t& eq) {
+    if constexpr (ZC >= 3) {
+        b = 0u;
+        eq = lop3<0x01>(lop3<0xFE>(V[0], V[1], V[2]), lop3<0xFE>(V[3], W[0], W[1]),
+                        W[2] | W[3]);  // ~(a | b | c)
+        return;
+    }
     b = 0u;
     eq = 0xFFFFFFFFu;
     const BlockBits f = bt[1];
 #pragma unroll
     for (int m = 3; m >= 0; --m) {
-        const uint32_t t = thr_word(c4, c8, c12, f, m);
+        const uint32_t t = thr_word_z<ZC>(c4, c8, c12, f, m);
         b = lop3<0x8E>(V[m], t, b);    // (~V & t) | (~(V ^ t) & b)
         eq = lop3<0x82>(V[m], t, eq);  // eq & ~(V ^ t)
     }
     const BlockBits e = bt[0];
 #pragma unroll
     for (int m = 3; m >= 0; --m) {
-        const uint32_t t = thr_word(c4, c8, c12, e, m);
+        const uint32_t t = thr_word_z<ZC>(c4, c8, c12, e, m);
         b = lop3<0x8E>(W[m], t, b);
         eq = lop3<0x82>(W[m], t, eq);
     }
@@ -391,6 +422,7 @@ __global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* c
         }
     };
     const uint32_t nh = 2u * r.stheta[i - 1];
+    const int zc = zero_classes3(thr[1], thr[2], thr[3]);
     if (nh > 0) build_tables(0u);
     __syncthreads();
 
@@ -405,45 +437,53 @@ __global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* c
         int k = 0;
         while (true) {
             int wq = 0;
+            // one copy of the walk per ZC (the same for the whole launch)
+            auto pass1 = [&](auto zc_tag) {
+                constexpr int ZC = decltype(zc_tag)::value;
 #pragma unroll 1
-            for (; k < S::ITERS && wq <= qflush; ++k) {
-                const int e = threadIdx.x + k * NT3;
-                const bool have = e < G * H;
-                // lanes past the work items run item 0 with no valid replica
-                const int ee = have ? e : 0;
-                const int g = ee / H, q = ee - g * H;
-                const uint2 en = ct[q];
-                uint32_t* la = lat + g * S::CELLS + (en.x & 0xFFFFu);
-                const uint32_t s = en.y;
-                const uint32_t vm = have ? sVm[g] : 0u;
-                const uint32_t w = la[0];
-                uint32_t ab[6];
-                bond_partners<L, EA>(la, EA ? cj[q] : make_uint2(0u, 0u), ab);
-                uint32_t need, c4, c8, c12;
-                classes3_w(w, ab, vm, need, c4, c8, c12);
-                const uint32_t A2s = sA2x[g] ^ s;
-                uint32_t B1, h0c, l0c;
-                {
-                    uint32_t h1b, l1b;
-                    mulhilo(PHILOX_M1, A2s, h1b, l1b);
-                    B1 = l1b;
-                    mulhilo(PHILOX_M0, h1b ^ B1k, h0c, l0c);
+                for (; k < S::ITERS && wq <= qflush; ++k) {
+                    const int e = threadIdx.x + k * NT3;
+                    const bool have = e < G * H;
+                    // lanes past the work items run item 0 with no valid replica
+                    const int ee = have ? e : 0;
+                    const int g = ee / H, q = ee - g * H;
+                    const uint2 en = ct[q];
+                    uint32_t* la = lat + g * S::CELLS + (en.x & 0xFFFFu);
+                    const uint32_t s = en.y;
+                    const uint32_t vm = have ? sVm[g] : 0u;
+                    const uint32_t w = la[0];
+                    uint32_t ab[6];
+                    bond_partners<L, EA>(la, EA ? cj[q] : make_uint2(0u, 0u), ab);
+                    uint32_t need, c4, c8, c12;
+                    classes3_w(w, ab, vm, need, c4, c8, c12);
+                    const uint32_t A2s = sA2x[g] ^ s;
+                    uint32_t B1, h0c, l0c;
+                    {
+                        uint32_t h1b, l1b;
+                        mulhilo(PHILOX_M1, A2s, h1b, l1b);
+                        B1 = l1b;
+                        mulhilo(PHILOX_M0, h1b ^ B1k, h0c, l0c);
+                    }
+                    uint32_t Wd[4], Vd[4];
+                    draw2_3(gt[g][0], gt[g][1], B1, h0c, l0c, p, Wd, Vd);
+                    uint32_t b, eq;
+                    cmp8_3<ZC>(c4, c8, c12, btab, Wd, Vd, b, eq);
+                    const uint32_t lt = b & need;
+                    const uint32_t und = eq & need;
+                    const bool undecided = und != 0u;
+                    const uint32_t ball = __ballot_sync(0xFFFFFFFFu, undecided);
+                    const int slot = undecided ? wq + __popc(ball & lml) : S::QW + lane;
+                    queue[slot] = make_uint4(A2s, und, lt, (uint32_t)ee);
+                    const uint32_t f = (~need | lt) & (undecided ? 0u : vm);
+                    if (have) store_site<L>(la, w ^ f, en.x >> 16);
+                    acc += (uint32_t)__popc(f);
+                    wq += __popc(ball);
                 }
-                uint32_t Wd[4], Vd[4];
-                draw2_3(gt[g][0], gt[g][1], B1, h0c, l0c, p, Wd, Vd);
-                uint32_t b, eq;
-                cmp8_3(c4, c8, c12, btab, Wd, Vd, b, eq);
-                const uint32_t lt = b & need;
-                const uint32_t und = eq & need;
-                const bool undecided = und != 0u;
-                const uint32_t ball = __ballot_sync(0xFFFFFFFFu, undecided);
-                const int slot = undecided ? wq + __popc(ball & lml) : S::QW + lane;
-                queue[slot] = make_uint4(A2s, und, lt, (uint32_t)ee);
-                const uint32_t f = (~need | lt) & (undecided ? 0u : vm);
-                if (have) store_site<L>(la, w ^ f, en.x >> 16);
-                acc += (uint32_t)__popc(f);
-                wq += __popc(ball);
-            }
+            };
+            if (zc == 0) pass1(IC<0>{});
+            else if (zc == 1) pass1(IC<1>{});
+            else if (zc == 2) pass1(IC<2>{});
+            else pass1(IC<3>{});
             // the warp's undecided sites, one per lane, from plane block 2 on
             __syncwarp();
             for (int e2 = lane; e2 < wq; e2 += 32) {

@@ -274,6 +274,29 @@ def test_3d_group_multiple_does_not_change_results(sides):
     g.close()
 
 
+@pytest.mark.parametrize("d,L,kind,R", [(2, 64, "ferro", 70), (2, 32, "ea", 100),
+                                        (3, 8, "ea", 130), (3, 12, "ferro", 40)])
+def test_steps_across_zero_top_threshold_bits(d, L, kind, R):
+    """The sweep kernels leave out the threshold terms of the energy classes whose
+    threshold exp(-beta dE) has eight zero top bits (below 1/256) in the two plane
+    blocks every site draws.  Steps on both sides of each boundary (2D: dE = 8 at
+    beta = ln 256 / 8, dE = 4 at ln 256 / 4; 3D also dE = 12 at ln 256 / 12) must
+    equal the oracle bit for bit."""
+    cpl, J = _couplings(d, L, kind)
+    c = math.log(256.0)
+    edges = [c / 12, c / 8, c / 4]
+    betas = np.array([0.0, 0.3] + [e + s for e in edges for s in (-0.01, 0.01)] + [2.5])
+    thetas = np.full(len(betas) - 1, 2, np.uint32)
+    gpu = pa.Population(d, L, R, betas, thetas, "systematic", 17, couplings=cpl)
+    orc = O.Run(d, L, J, R, betas, thetas, O.RESAMPLERS["systematic"], 17)
+    N = L ** d
+    for i in range(len(betas) - 1):
+        gpu.step(1)
+        assert orc.step() == 0
+        compare_step(gpu, orc, N, f"step {i + 1} beta {betas[i + 1]:.3f}")
+    gpu.close()
+
+
 @pytest.mark.parametrize("d,L,R,kind,method,bf,caps", [
     (2, 64, 96, "ferro", "systematic", 1.0, (0, 32)),
     (3, 6, 150, "ea", "poisson", 3.0, (0, 4)),
