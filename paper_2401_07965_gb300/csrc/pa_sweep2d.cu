@@ -442,7 +442,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
         int k = 0;
         while (true) {
             int wq = 0;
-            // one copy of the walk per ZC (the same for the whole launch)
+            // a copy of the walk for ZC = 0 and one for ZC >= 1 (the same for the whole
+            // launch; a third copy for ZC = 2, which drops the dE = 4 term as well,
+            // slowed the ZC = 0 walk more than it saves above beta = ln 256 / 4)
             auto pass1 = [&](auto zc_tag) {
                 constexpr int ZC = decltype(zc_tag)::value;
 #pragma unroll 1
@@ -452,8 +454,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
                                           wq, acc);
             };
             if (zc == 0) pass1(IC<0>{});
-            else if (zc == 1) pass1(IC<1>{});
-            else pass1(IC<2>{});
+            else pass1(IC<1>{});
             site_pass2<L, EA>(lat, jw, queue, wq, lane, A2x, B1k, vmask, hs.tab, p, acc);
             if (k == ITERS) break;
         }
@@ -467,8 +468,14 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
         __syncthreads();
     }
 
-    // measurement: unsatisfied bonds U and up-count per replica, write back
-    int32_t U = 0, nup = 0;
+    // measurement: unsatisfied bonds U and up-count per replica, write back.  The
+    // thread's unsatisfied-bond words go into a bit-sliced counter (at most 2 per
+    // site word it visits), summed per replica at the end.
+    constexpr int CB = vc_bits(2 * 4 * ((W / 4 + NW - 1) / NW));
+    uint32_t ucnt[CB];
+#pragma unroll
+    for (int j = 0; j < CB; ++j) ucnt[j] = 0u;
+    int32_t nup = 0;
     for (int c4 = warp; 4 * c4 < W; c4 += NW) {
         uint32_t out[4];
 #pragma unroll
@@ -485,12 +492,13 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 80)) k_sweep2d(KParams p) {
                 P0 ^= J.x;
                 P1 ^= J.z;
             }
-            U += __popc(transpose32(P0, lane)) + __popc(transpose32(P1, lane));
+            vc_add2(ucnt, P0, P1);
         }
         if (valid)
             reinterpret_cast<uint4*>(dst + (size_t)(base + lane) * r.Wp)[c4] =
                 make_uint4(out[0], out[1], out[2], out[3]);
     }
+    const int32_t U = vc_total(ucnt, lane);
     atomicAdd(&sU[lane], U);
     atomicAdd(&sNup[lane], nup);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

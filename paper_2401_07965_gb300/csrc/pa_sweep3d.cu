@@ -520,8 +520,9 @@ __global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* c
     for (int k = warp; k < G * (WP / 4); k += NW) {
         const int g = k / (WP / 4), c4 = k % (WP / 4);
         const uint32_t* lg = lat + g * S::CELLS;
-        int32_t U = 0, nup = 0;
+        int32_t nup = 0;
         uint32_t out[4];
+        uint32_t ucnt[4] = {0u, 0u, 0u, 0u};  // bit-sliced count of up to 12 bonds
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int b = 4 * c4 + m;
@@ -546,10 +547,10 @@ __global__ void __launch_bounds__(NT3, 6) k_sweep3d(KParams p, const uint32_t* c
                 const uint32_t tw = transpose32(w, lane);
                 out[m] = tw;
                 nup += __popc(tw);
-                U += __popc(transpose32(P0, lane)) + __popc(transpose32(P1, lane)) +
-                     __popc(transpose32(P2v, lane));
+                vc_add3(ucnt, P0, P1, P2v);
             }
         }
+        const int32_t U = vc_total(ucnt, lane);
         const uint32_t slot = (gfirst + g) * 32u + lane;
         if (slot < R)
             reinterpret_cast<uint4*>(dst + (size_t)slot * r.Wp)[c4] =

@@ -28,6 +28,51 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
     return x;
 }
 
+// Bit-sliced counters for the measurement: plane j of the CB words holds bit j
+// of one count per bit position (replica), so adding one-bit words costs a few
+// logic operations and the per-replica sums need one transpose per plane
+// instead of one per added word.
+__host__ __device__ constexpr int vc_bits(int n) { return n > 0 ? 1 + vc_bits(n >> 1) : 0; }
+
+// c += a + b (per bit position)
+template <int CB>
+__device__ __forceinline__ void vc_add2(uint32_t (&c)[CB], uint32_t a, uint32_t b) {
+    uint32_t carry = lop3<0xE8>(c[0], a, b);  // majority: the carry of a full adder
+    c[0] = lop3<0x96>(c[0], a, b);
+#pragma unroll
+    for (int j = 1; j < CB; ++j) {
+        const uint32_t t = c[j] & carry;
+        c[j] ^= carry;
+        carry = t;
+    }
+}
+
+// c += a + b + d (per bit position), CB >= 2
+template <int CB>
+__device__ __forceinline__ void vc_add3(uint32_t (&c)[CB], uint32_t a, uint32_t b, uint32_t d) {
+    static_assert(CB >= 2, "vc_add3 needs two planes");
+    const uint32_t sm = lop3<0x96>(a, b, d), k = lop3<0xE8>(a, b, d);  // a+b+d = sm + 2k
+    const uint32_t k2 = c[0] & sm;                                      // c0+sm = (c0^sm) + 2k2
+    c[0] ^= sm;
+    uint32_t carry = lop3<0xE8>(c[1], k, k2);
+    c[1] = lop3<0x96>(c[1], k, k2);
+#pragma unroll
+    for (int j = 2; j < CB; ++j) {
+        const uint32_t t = c[j] & carry;
+        c[j] ^= carry;
+        carry = t;
+    }
+}
+
+// lane r: the sum over the warp's lanes of their counts at bit position r
+template <int CB>
+__device__ __forceinline__ int32_t vc_total(const uint32_t (&c)[CB], int lane) {
+    int32_t u = 0;
+#pragma unroll
+    for (int j = 0; j < CB; ++j) u += __popc(transpose32(c[j], lane)) << j;
+    return u;
+}
+
 // ---------------------------------------------------------------------------
 // Bit-plane uniforms.  The uniform u of replica r (slot base + r) at site s has
 // bit 31 - p equal to bit r of plane word p, the lane p & 3 of the Philox draw
