@@ -234,9 +234,9 @@ __device__ __forceinline__ uint32_t sign_of_byte(uint32_t v) {
     return r;
 }
 
-// the six bond planes of a site: j holds its bond signs as byte sign bits, x
-// bytes 0-3 the bonds to +x, -x, +y, -y and y bytes 0-1 those to +z, -z
 // the six bond partners of a site: neighbour words, XOR the bond signs for EA
+// (j holds them as byte sign bits: x bytes 0-3 the bonds to +x, -x, +y, -y and
+// y bytes 0-1 those to +z, -z)
 template <int L, bool EA>
 __device__ __forceinline__ void bond_partners(const uint32_t* la, uint2 j, uint32_t (&a)[6]) {
     constexpr int PP = L + 2, P2 = PP * PP;
