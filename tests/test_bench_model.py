@@ -86,3 +86,19 @@ def test_mean_over_steps_weights_steps_equally():
     a, b = bench.pipes_model(2, 0), bench.pipes_model(2, 1)
     for k in m:
         assert m[k][0] == pytest.approx((3 * a[k][0] + b[k][0]) / 4)
+
+
+def test_clock_summary_reads_throttle_reasons():
+    c = bench.ClockSampler(0)
+    assert c.summary()["reasons"] == ["unavailable"]
+    c.lines = [
+        "0, 2070, 2070, 850.10, 0x0000000000000000, Not Active, Not Active, Not Active, "
+        "Not Active",
+        "0, 1980, 2070, 1400.00, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, 2040, 2070, 1390.00, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+    ]
+    s = c.summary()
+    assert s["samples"] == 3
+    assert s["sm_mhz"] == 2040 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
