@@ -1,4 +1,4 @@
-"""The sweep roofline model of bench.py (host logic, no GPU).
+"""Host logic of bench.py (no GPU): the sweep roofline model and the clock summary.
 
 The model counts, per site word (one site of 32 replicas), the integer work of the
 bit-plane Metropolis test with an ideal stop at the first deciding plane block.
